@@ -1,0 +1,398 @@
+"""Throughput of the importance-sampled first-passage-time hot path on GB300.
+
+One step = one batched call of the C ABI over the whole workload: the
+persistent Euler–Maruyama stepper for every run of every parameter set plus
+the per-set weighted histograms.  Default workload: the drift-dominated bias
+ladder, quadratic inflation m = 0.01, phi_in = 6, dN = 1e-3,
+b in {0, 0.5, 1, 2, 4} x 2^22 runs in one launch, binary32 state with a
+compensated log-weight sum, 400 bins on (7, 10].
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("trajectory steps/s and far-tail effective samples/s at 1 GB300 vs FP64 plain; "
+          "% issue roofline")
+
+# Algorithmic warp-instructions per Euler–Maruyama step of the binary32 stepper
+# (hand count of the work the step needs; derivation in the design doc): Philox
+# 38 per 4 steps, Box–Muller 15 per 2 steps, update + block minimum + noise sum 7.
+ALG_INST_PER_STEP = 38 / 4 + 15 / 2 + 7
+MUFU_PER_STEP = 3.0  # lg2 + sqrt + sin + cos per 2 steps, rcp per step
+ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 schedulers)
+MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="drift_ladder",
+                    choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's runs")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--block-dim", type=int, default=0)
+    ap.add_argument("--k-steps", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_workload(name, scale):
+    from paper_2206_11234_gb300 import workloads as W
+    return {"drift_ladder": W.drift_dominated_ladder, "quadratic_b1": W.quadratic_fixed_b,
+            "batched_uneven": W.batched_uneven, "diffusion_wall": W.diffusion_wall}[name](scale)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def tail_neff(N, lw, specs, tail_N):
+    """n_eff = P^2 / Var(P) of the weighted estimator of P(N > tail_N), per set."""
+    import torch
+    out = []
+    off = 0
+    for s in specs:
+        n = s.n_traj
+        x = torch.where(N[off:off + n] > tail_N, torch.exp(lw[off:off + n]), torch.zeros_like(lw[off:off + n]))
+        P = x.mean().item()
+        var = x.var().item() / n if n > 1 else float("inf")
+        out.append({"b": s.b, "P": P, "n_eff": (P * P / var) if var > 0 else 0.0})
+        off += n
+    return out
+
+
+def cpu_oracle_rate(workload, seconds, threads=None):
+    """The FP64 oracle on the host cores (threads calling the C oracle on
+    disjoint run ranges; ctypes releases the GIL).  Returns (steps/s, cores,
+    sample description)."""
+    import numpy as np
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    specs = workload.sets
+    lock = threading.Lock()
+    tally = {"steps": 0, "runs": 0}
+    deadline = time.perf_counter() + seconds
+    next_index = [0] * len(specs)
+
+    def worker(tid):
+        chunk = 64
+        j = tid % len(specs)
+        while time.perf_counter() < deadline:
+            s = specs[j]
+            with lock:
+                start = next_index[j]
+                next_index[j] += chunk
+            r = oracle.make_run(model=s.model, m=s.m, a0=s.a0, s0=s.s0, phi_in=s.phi_in,
+                                phi_end=s.phi_end, phi_uv=s.phi_uv, dN=s.dN, b=s.b, n_max=s.n_max,
+                                seed=workload.seed, set_id=s.set_id, traj_offset=start)
+            _, _, st = oracle.simulate(r, chunk)
+            with lock:
+                tally["steps"] += int(st.sum())
+                tally["runs"] += chunk
+            j = (j + 1) % len(specs)
+
+    oracle.lib()  # build/load before timing
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker, args=(i,)) for i in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    sample = (f"{tally['runs']} runs ({tally['steps']} steps) drawn round-robin from the "
+              f"{len(specs)} sets of the same workload, {dt:.1f} s wall on {threads} threads")
+    return tally["steps"] / dt, threads, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, args.scale)
+    per = max(args.cpu_seconds / max(args.steps, 1), 1.0)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, min(per, 2.0))
+    rates = []
+    t0 = time.perf_counter()
+    cores = 1
+    sample = ""
+    for _ in range(args.steps):
+        r, cores, sample = cpu_oracle_rate(wl, per)
+        rates.append(r)
+    total_t = time.perf_counter() - t0
+    v = statistics.mean(rates)
+    line = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "precision": "f64 (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2206_11234_gb300 import native as nat
+    from paper_2206_11234_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    wl = make_workload(args.workload, args.scale)
+    # weak scaling: each rank simulates its own disjoint id range of every set
+    for s in wl.sets:
+        s.traj_offset = rank * s.n_traj
+    specs = wl.sets
+    n = wl.n_total
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    N = torch.empty(n, dtype=torch.float64, device=dev)
+    lw = torch.empty(n, dtype=torch.float64, device=dev)
+    nbins = sum(s.n_bins for s in specs)
+    bins = nat.empty_bins(nbins, dev)
+    counts = nat.empty_counts(len(specs), dev)
+    steps_ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    sets = nat.make_sets(specs)
+    s0 = specs[0]
+
+    def params(prec, steps_out=None):
+        return nat.make_params(model=s0.model, precision=prec, m=s0.m, a0=s0.a0, s0=s0.s0,
+                               n_max=s0.n_max, block_dim=args.block_dim, k_steps=args.k_steps,
+                               stream=stream, steps_out=steps_out)
+
+    p = params(wl.precision, steps_ctr)
+
+    def one_step(seed):
+        nat.fpt_simulate_batch(p, sets, seed, N, lw, bins, counts)
+
+    for i in range(args.warmup):
+        one_step(1000 + i)
+    torch.cuda.synchronize()
+    steps_ctr.zero_()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            one_step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    my_steps = int(steps_ctr.item())
+    t = torch.tensor([ms, float(my_steps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max, total_steps = tmax[0].item(), tsum[1].item()
+    else:
+        ms_max, total_steps = ms, float(my_steps)
+    value = total_steps / (ms_max / 1e3)
+
+    # the stepper kernel alone (CUDA events on the launching stream), for the roofline
+    ms_stepper = None
+    if rank == 0:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        steps_ctr.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            nat.fpt_simulate_batch(p, sets, i, N, lw, None, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_stepper = e0.elapsed_time(e1) / args.steps
+        stepper_steps = int(steps_ctr.item()) / args.steps
+
+    extra = {}
+    if rank == 0:
+        # far-tail effective samples (E = {N > tail_N}) of the last timed step's runs
+        nat.fpt_simulate_batch(p, sets, args.steps - 1, N, lw, bins, counts)
+        if wl.tail_N is not None:
+            ne = tail_neff(N, lw, specs, wl.tail_N)
+            best = max(ne, key=lambda r: r["n_eff"])
+            extra["tail"] = {"event": f"N > {wl.tail_N}", "per_set": ne,
+                             "best_n_eff_per_s": best["n_eff"] / (ms_max / 1e3 / args.steps),
+                             "best_b": best["b"]}
+        # FP64 GPU plain on a bounded sample of the same workload (speed reference)
+        if not args.no_f64:
+            frac = min(1.0, 2**16 * len(specs) / n)
+            wl64 = make_workload(args.workload, args.scale * frac)
+            p64 = params("f64", steps_ctr)
+            n64 = wl64.n_total
+            N64 = torch.empty(n64, dtype=torch.float64, device=dev)
+            l64 = torch.empty(n64, dtype=torch.float64, device=dev)
+            s64 = nat.make_sets(wl64.sets)
+            nat.fpt_simulate_batch(p64, s64, 0, N64, l64, None, None)
+            steps_ctr.zero_()
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nat.fpt_simulate_batch(p64, s64, 1, N64, l64, None, None)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            extra["f64_gpu_plain"] = {"value": int(steps_ctr.item()) / (a.elapsed_time(b_) / 1e3),
+                                      "unit": "steps/s", "runs": n64}
+            del N64, l64
+
+    # end to end through the host-buffer entry (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hN = torch.empty(n, dtype=torch.float64).pin_memory()
+        hl = torch.empty(n, dtype=torch.float64).pin_memory()
+        hb = torch.empty((nbins, 6), dtype=torch.float64).pin_memory()
+        hc = torch.empty((len(specs), 4), dtype=torch.int64).pin_memory()
+        pe = params(wl.precision, steps_ctr)
+        nat.fpt_simulate_batch_host(pe, sets, 7, hN, hl, hb, hc)
+        steps_ctr.zero_()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            nat.fpt_simulate_batch_host(pe, sets, i, hN, hl, hb, hc)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt, float(steps_ctr.item())], dtype=torch.float64, device=dev)
+        if world > 1:
+            t1 = tt.clone()
+            dist.all_reduce(t1, op=dist.ReduceOp.MAX)
+            t2 = tt.clone()
+            dist.all_reduce(t2, op=dist.ReduceOp.SUM)
+            dt, es = t1[0].item(), t2[1].item()
+        else:
+            es = tt[1].item()
+        import ctypes
+        h2d = ctypes.sizeof(nat.FptSet) * len(specs) + ctypes.sizeof(nat.FptParams)
+        d2h = 2 * 8 * n + 48 * nbins + 32 * len(specs)
+        e2e = {"value": es / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    issue_peak = n_sm * ISSUE_PER_SM_CLK * f_max  # warp-instructions/s
+    steps_peak = min(issue_peak / ALG_INST_PER_STEP, n_sm * MUFU_PER_SM_CLK * f_max / MUFU_PER_STEP) * 32
+    achieved_steps = stepper_steps / (ms_stepper / 1e3)
+    roof = {"bound": "alu", "achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9,
+            "peak": issue_peak / 1e9, "unit": "Gwarp-inst/s (algorithmic)",
+            "frac": achieved_steps / steps_peak, "traffic": None,
+            "kernel": "stepper_kernel<float, F32_KAHAN, QUADRATIC, no wall, 16>",
+            "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
+            "peak_source": f"{n_sm} SMs x 4 issue/clk x {f_max / 1e6:.0f} MHz (max SM clock, "
+                           "MEASURED_PEAKS.json); MUFU co-bound 16/clk/SM"}
+    cpu = None
+    if not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl.precision != "f64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "precision": wl.precision, "runs_per_gpu": n,
+                   "sets": len(specs), "l2": "outputs (16 B/run) exceed L2; no inputs besides parameters",
+                   "parallelism": f"dp{world} (disjoint run ids per GPU)"},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    line.update(extra)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * fpt.h — C ABI of the GB300 (sm_103a) importance-sampled first-passage-time
+ * library.
+ *
+ * The method is that of Jackson, Assadullahi, Koyama, Vennin, Wands,
+ * "Numerical simulations of stochastic inflation using importance sampling"
+ * (arXiv:2206.11234), §2:
+ *   - runs of the 1-D Langevin equation dphi/dN = D(phi) + S(phi) xi
+ *     (§2.1 Eq. (7)) with the drift shifted by a bias B (§2.2 Eq. (10)),
+ *     integrated by Euler–Maruyama (§2.2 Eq. (11)) until phi first reaches
+ *     phi_end (§2.1, below Eq. (8));
+ *   - for slow-roll inflation D = -V'/(3H^2), S = H/(2 pi) (§2.3 Eq. (17))
+ *     with V = m^2 phi^2 / 2 (§3 Eq. (25)) and M_Pl = 1, so D = -2/phi and
+ *     S = m phi / (2 pi sqrt 6); the bias is B = b S (§2.3 Eq. (18), f = S);
+ *   - each run records its first-passage time N and its log importance weight
+ *     ln w = ln(p_T/p_S) = -sum_m (B/S^2)[B dN/2 + S xi_m sqrt(dN)]
+ *     (§2.2 Eqs. (12)-(14); Eq. (15) is printed with the opposite overall sign,
+ *     which contradicts Eqs. (13)-(14));
+ *   - an optional reflecting wall at phi_uv (§2.3 below Eq. (19), §3);
+ *   - the records are binned into a weighted histogram (§2.1 Eq. (9),
+ *     §2.2 Eq. (16)).
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller unless the
+ *     name ends in _host.  Outputs are indexed by trajectory, whatever order
+ *     the GPU finishes them in, so results are deterministic.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; the call then reads back a device status word, which
+ *     synchronises that stream only.
+ *   - Return value: FPT_OK (0) or a negative FPT_E* code.  Argument errors are
+ *     detected on the host before any GPU work is enqueued.  fpt_strerror()
+ *     names a code; fpt_last_error() describes the last failure of the calling
+ *     thread.
+ *   - Random numbers: xi for steps 4k..4k+3 of trajectory i come from one
+ *     Philox4x32-10 block (Salmon et al., SC'11) with counter
+ *     (k, i_lo, i_hi, set_id) and key (seed_lo, seed_hi), mapped to normals by
+ *     Box–Muller.  Any run can be reproduced from (seed, set_id, i) alone, so
+ *     an id range can be split across calls or GPUs (traj_offset) with
+ *     bit-identical results.
+ *   - A run still inflating after ceil(n_max/dN) steps is censored: N = +inf,
+ *     ln w = its weight at that step (E[w] = 1 still holds).
+ */
+#ifndef FPT_H
+#define FPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPT_ABI_VERSION 1
+
+/* return codes */
+#define FPT_OK 0
+#define FPT_EINVAL (-1)          /* invalid argument (checked on the host) */
+#define FPT_ECUDA (-2)           /* a CUDA runtime call failed */
+#define FPT_ENOMEM (-3)          /* device allocation failed */
+#define FPT_EUNSUPPORTED (-4)    /* valid but not provided (e.g. FP64 with the MLP bias) */
+#define FPT_EDEVICE_STATUS (-5)  /* a kernel reported an internal error (bounded wait expired) */
+
+/* drift/noise model */
+#define FPT_MODEL_QUADRATIC 0 /* D = -2/phi, S = m phi/(2 pi sqrt 6): §2.3 Eq. (17) + §3 Eq. (25) */
+#define FPT_MODEL_CONSTANT 1  /* D = a0, S = s0: constant drift and noise (inverse-Gaussian test model) */
+
+/* arithmetic of the stepper */
+#define FPT_PREC_F64 0        /* everything binary64 (reference mode, per-run parity with the FP64 oracle) */
+#define FPT_PREC_F32_KAHAN 1  /* binary32 state; ln w from binary32 block sums + compensated (Kahan) running sum */
+#define FPT_PREC_F32_F64ACC 2 /* binary32 state; ln w running sum and crossing interpolation in binary64 */
+
+/* bias B = b S */
+#define FPT_BIAS_CONST 0 /* b constant */
+#define FPT_BIAS_MLP 2   /* b = MLP(phi, N_elapsed), held for k_eval steps (see fpt_mlp_params) */
+
+#define FPT_MAX_SETS 64       /* parameter sets per batched launch */
+#define FPT_MAX_HIST_BINS 4096 /* n_sub * n_bins per histogram */
+
+typedef struct fpt_params {
+    int32_t abi_version; /* must be FPT_ABI_VERSION */
+    int32_t model;       /* FPT_MODEL_* */
+    int32_t precision;   /* FPT_PREC_* */
+    int32_t bias_kind;   /* FPT_BIAS_* */
+    double m;            /* inflaton mass (quadratic model), > 0 */
+    double a0, s0;       /* constant model: drift and noise amplitude (s0 > 0) */
+    double n_max;        /* censoring time, finite and > 0 */
+    const void* mlp;     /* FPT_BIAS_MLP: device pointer to an fpt_mlp_params */
+    int32_t k_eval;      /* FPT_BIAS_MLP: steps between bias evaluations (0 = 32) */
+    int32_t block_dim;   /* threads per block of the stepper (0 = autotuned or default) */
+    int32_t k_steps;     /* steps per scheduling block of the stepper (0 = autotuned or default) */
+    uint32_t set_id;     /* Philox counter word 3 (fpt_simulate only) */
+    uint64_t traj_offset; /* global id of the first trajectory (fpt_simulate only) */
+    void* stream;        /* cudaStream_t */
+    uint64_t* steps_out; /* optional device counter: the number of Euler–Maruyama steps taken is ADDED to it */
+} fpt_params;
+
+/* Simulate n_traj runs of one parameter set (§2.2 Eqs. (10)-(15)).
+ *   phi_in, phi_end : start and end of inflation; phi_in <= phi_end gives N = 0, ln w = 0
+ *   phi_uv          : reflecting wall, >= phi_in, or +INFINITY for none
+ *   dN              : time step (e-folds), > 0
+ *   bias            : b (FPT_BIAS_CONST), ignored for FPT_BIAS_MLP
+ *   out_N, out_logw : device double[n_traj]; out_N[i] = +inf when censored.
+ * n_traj = 0 is a no-op.  Errors: FPT_EINVAL, FPT_EUNSUPPORTED, FPT_ECUDA,
+ * FPT_ENOMEM, FPT_EDEVICE_STATUS. */
+int fpt_simulate(const fpt_params* p, int64_t n_traj, double phi_in, double phi_end, double phi_uv,
+                 double dN, double bias, uint64_t seed, double* out_N, double* out_logw);
+
+/* One parameter set of a batched launch (host memory). */
+typedef struct fpt_set {
+    double phi_in, phi_end, phi_uv; /* as in fpt_simulate */
+    double m;                        /* mass (quadratic model; the constant model uses p->a0, p->s0) */
+    double b;                        /* bias amplitude */
+    double dN;                       /* time step */
+    double n_max;                    /* censoring time */
+    int64_t n_traj;                  /* runs in this set (>= 0) */
+    uint64_t traj_offset;            /* global id of this set's first run */
+    uint32_t set_id;                 /* Philox counter word 3 */
+    int32_t n_bins;                  /* histogram bins for this set (fpt_simulate_batch with bins) */
+    double hist_lo, hist_hi;         /* histogram range (lo, hi] */
+} fpt_set;
+
+/* Weighted-histogram bin (§2.1 Eq. (9), §2.2 Eq. (16)) with max-shifted sums so
+ * that weights spanning hundreds of e-folds stay representable:
+ *   sum_i w_i   = exp(max_lw) * s1,   sum_i w_i^2 = exp(2 max_lw) * s2,
+ *   l1 = sum ln w_i, l2 = sum (ln w_i)^2, count = n_j.  Empty bin: max_lw = -inf. */
+typedef struct fpt_bin {
+    double max_lw, s1, s2, l1, l2;
+    int64_t count;
+} fpt_bin;
+
+/* Counters of a histogram: runs with N <= lo, finite N > hi, N not finite
+ * (censored), and all runs. */
+typedef struct fpt_hist_counts {
+    int64_t under, over, censored, total;
+} fpt_hist_counts;
+
+/* Simulate n_sets parameter sets in ONE persistent launch (finished lanes
+ * refill from a global ticket counter across all sets).  Set s writes
+ * out_N/out_logw[off_s .. off_s + n_traj_s), off_s = sum_{t<s} n_traj_t.
+ * If out_bins is non-NULL the per-set histograms are built in the same call:
+ * set s fills out_bins[boff_s .. boff_s + n_bins_s), boff_s = sum_{t<s} n_bins_t,
+ * and out_counts[s] (device).
+ * sets: host array, 1 <= n_sets <= FPT_MAX_SETS; p->set_id and p->traj_offset
+ * are ignored (each set carries its own). */
+int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
+                       double* out_N, double* out_logw, fpt_bin* out_bins,
+                       fpt_hist_counts* out_counts);
+
+/* Weighted histogram of n records.  Bins (lo + j d, lo + (j+1) d],
+ * d = (hi - lo)/n_bins, j = ceil((N - lo)/d) - 1 clamped to [0, n_bins).
+ * Record i (global id id_offset + i) goes to subset (id_offset + i) mod n_sub
+ * (jackknife subsets, §2.1); bins[s * n_bins + j].  The outputs are
+ * overwritten.  1 <= n_bins, 1 <= n_sub, n_sub * n_bins <= FPT_MAX_HIST_BINS,
+ * lo < hi finite. */
+int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo,
+                  double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
+                  fpt_hist_counts* counts, void* stream);
+
+/* End-to-end call with HOST buffers: copies nothing in but the parameters,
+ * runs fpt_simulate_batch with bins on a private device workspace and copies
+ * (N, ln w) and the histograms back to host_N/host_logw (may be NULL to skip)
+ * and host_bins/host_counts.  Device memory is allocated and freed inside. */
+int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
+                            double* host_N, double* host_logw, fpt_bin* host_bins,
+                            fpt_hist_counts* host_counts);
+
+/* Diagnostic: the unit normals xi_{4k} .. xi_{4k+3} for k = k0 .. k0 + n_blocks - 1
+ * of run `traj` of set `set_id` (exactly what the stepper draws; §2.1 below
+ * Eq. (8)), written to the device array out as double (FPT_PREC_F64) or float
+ * (the binary32 precisions), 4 * n_blocks values.  precision =
+ * FPT_NORMALS_RAW_BITS writes the 4 Philox words of each block as uint32
+ * instead.  Synchronises `stream`. */
+#define FPT_NORMALS_RAW_BITS 3
+int fpt_normals(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k0, int64_t n_blocks,
+                int32_t precision, void* out, void* stream);
+
+/* Human-readable name of a return code (static string). */
+const char* fpt_strerror(int code);
+/* Description of the last failure in the calling thread ("" if none). */
+const char* fpt_last_error(void);
+/* Library ABI version (FPT_ABI_VERSION of the build). */
+int fpt_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPT_H */

@@ -1,0 +1,41 @@
+// Internal helpers shared by the C ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "fpt.h"
+#include "histogram.h"
+#include "stepper_launch.h"
+
+namespace fpt {
+
+// Record a failure message for fpt_last_error() and return `code`.
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int device_sm_count(int* n_sm);
+int check_params(const fpt_params* p);
+
+// Host-side image of one batched call.
+struct Prepared {
+    std::vector<SetConst> sets;
+    std::vector<HistSeg> segs;
+    unsigned long long n_total;
+    bool wall;
+    int max_nb;
+    long long max_n;
+    long long total_bins;
+};
+
+struct WorkspaceLayout {
+    size_t off_scratch, off_sets, off_segs, bytes;
+};
+
+int prepare(const fpt_params* p, const fpt_set* sets, int n_sets, bool with_hist, Prepared* P);
+void workspace_layout(const Prepared& P, WorkspaceLayout* L);
+void workspace_image(const Prepared& P, const WorkspaceLayout& L, std::vector<unsigned char>* img);
+int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L, unsigned char* ws,
+                uint64_t seed, double* out_N, double* out_logw, fpt_bin* bins, fpt_hist_counts* counts,
+                cudaStream_t stream);
+
+}  // namespace fpt

@@ -1,0 +1,36 @@
+// Host/device layout of the stepper's per-set constants and its scratch words.
+#pragma once
+#include <cstdint>
+
+#include "fpt.h"
+
+namespace fpt {
+
+constexpr int kStepperMaxThreads = 512;
+
+// Per parameter set, prepared on the host (binary64 originals and the
+// binary32 step constants), copied to shared memory by every block.
+struct SetConst {
+    double phi_in, phi_end, phi_uv, twouv;  // twouv = 2 phi_uv (reflection phi -> 2 phi_uv - phi)
+    double dN, sq, b;                       // sq = sqrt(dN)
+    double cm;                              // quadratic: c0 m, c0 = 1/(2 pi sqrt 6); constant model: s0
+    double a0;                              // constant model drift
+    double lw_bsq, lw_half_b2dN;            // ln w = -lw_bsq * W - lw_half_b2dN * M
+    long long first;                        // index of this set's first record
+    unsigned long long traj_offset;         // Philox id of this set's first run
+    int m_max;                              // censoring cap in steps
+    uint32_t set_id;                        // Philox counter word 3
+    float f_phi_in, f_phi_end, f_twouv;
+    float f_c1, f_c2, f_c3;                 // binary32 step constants (see ModelStep)
+    float pad_[2];
+};
+
+// Device scratch of one stepper launch (zeroed before the launch).
+struct StepperScratch {
+    unsigned long long ticket;  // next record index to hand out
+    unsigned long long steps;   // total Euler–Maruyama steps taken
+    unsigned int status;        // error flags (0 = ok)
+    unsigned int pad_;
+};
+
+}  // namespace fpt

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/fpt.h (argument marshalling only).
+
+Every function forwards to the CUDA library libfpt_gb300.so; there is no
+fallback: if the library is missing or cannot be loaded, importing this module
+raises.  Device arrays are torch CUDA tensors (torch provides device memory and
+streams); their data pointers are passed through unchanged.
+"""
+import ctypes
+import math
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+FPT_ABI_VERSION = 1
+FPT_OK = 0
+FPT_EINVAL = -1
+FPT_ECUDA = -2
+FPT_ENOMEM = -3
+FPT_EUNSUPPORTED = -4
+FPT_EDEVICE_STATUS = -5
+
+MODEL_QUADRATIC = 0
+MODEL_CONSTANT = 1
+PREC_F64 = 0
+PREC_F32_KAHAN = 1
+PREC_F32_F64ACC = 2
+PRECISIONS = {"f64": PREC_F64, "f32_kahan": PREC_F32_KAHAN, "f32_f64acc": PREC_F32_F64ACC}
+BIAS_CONST = 0
+BIAS_MLP = 2
+MAX_SETS = 64
+MAX_HIST_BINS = 4096
+
+
+class FptParams(ctypes.Structure):
+    _fields_ = [
+        ("abi_version", ctypes.c_int32),
+        ("model", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("bias_kind", ctypes.c_int32),
+        ("m", ctypes.c_double),
+        ("a0", ctypes.c_double),
+        ("s0", ctypes.c_double),
+        ("n_max", ctypes.c_double),
+        ("mlp", ctypes.c_void_p),
+        ("k_eval", ctypes.c_int32),
+        ("block_dim", ctypes.c_int32),
+        ("k_steps", ctypes.c_int32),
+        ("set_id", ctypes.c_uint32),
+        ("traj_offset", ctypes.c_uint64),
+        ("stream", ctypes.c_void_p),
+        ("steps_out", ctypes.c_void_p),
+    ]
+
+
+class FptSet(ctypes.Structure):
+    _fields_ = [
+        ("phi_in", ctypes.c_double),
+        ("phi_end", ctypes.c_double),
+        ("phi_uv", ctypes.c_double),
+        ("m", ctypes.c_double),
+        ("b", ctypes.c_double),
+        ("dN", ctypes.c_double),
+        ("n_max", ctypes.c_double),
+        ("n_traj", ctypes.c_int64),
+        ("traj_offset", ctypes.c_uint64),
+        ("set_id", ctypes.c_uint32),
+        ("n_bins", ctypes.c_int32),
+        ("hist_lo", ctypes.c_double),
+        ("hist_hi", ctypes.c_double),
+    ]
+
+
+class FptBin(ctypes.Structure):
+    _fields_ = [("max_lw", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double),
+                ("l1", ctypes.c_double), ("l2", ctypes.c_double), ("count", ctypes.c_int64)]
+
+
+class FptHistCounts(ctypes.Structure):
+    _fields_ = [("under", ctypes.c_int64), ("over", ctypes.c_int64), ("censored", ctypes.c_int64),
+                ("total", ctypes.c_int64)]
+
+
+BIN_FIELDS = 6  # an fpt_bin is 6 x 8 bytes: view bins as float64[n, 6] (count as int64 bits)
+
+
+class FptError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _load():
+    path = os.path.join(HERE, "libfpt_gb300.so")
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2206_11234_gb300/build.py "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    if not _build.up_to_date():
+        raise ImportError(f"{path} is older than its sources: rebuild it")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, d, i32, i64, u32, u64 = (ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
+                                 ctypes.c_uint32, ctypes.c_uint64)
+    L.fpt_simulate.argtypes = [P(FptParams), i64, d, d, d, d, d, u64, vp, vp]
+    L.fpt_simulate_batch.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
+    L.fpt_simulate_batch_host.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
+    L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
+    L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
+    L.fpt_strerror.restype = ctypes.c_char_p
+    L.fpt_strerror.argtypes = [ctypes.c_int]
+    L.fpt_last_error.restype = ctypes.c_char_p
+    L.fpt_abi_version.restype = ctypes.c_int
+    for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
+                 "fpt_normals"):
+        getattr(L, name).restype = ctypes.c_int
+    if L.fpt_abi_version() != FPT_ABI_VERSION:
+        raise ImportError("libfpt_gb300.so ABI version mismatch")
+    return L
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != FPT_OK:
+        raise FptError(rc, f"{lib.fpt_strerror(rc).decode()}: {lib.fpt_last_error().decode()}")
+
+
+def _dptr(t: Optional[torch.Tensor], dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_params(*, model=MODEL_QUADRATIC, precision=PREC_F64, m=1.0, a0=0.0, s0=0.0, n_max,
+                block_dim=0, k_steps=0, set_id=0, traj_offset=0, stream=None,
+                steps_out: Optional[torch.Tensor] = None) -> FptParams:
+    p = FptParams()
+    p.abi_version = FPT_ABI_VERSION
+    p.model = model
+    p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    p.bias_kind = BIAS_CONST
+    p.m, p.a0, p.s0, p.n_max = m, a0, s0, n_max
+    p.mlp = None
+    p.k_eval = 0
+    p.block_dim, p.k_steps = block_dim, k_steps
+    p.set_id, p.traj_offset = set_id, traj_offset
+    p.stream = _stream(stream)
+    p.steps_out = None if steps_out is None else steps_out.data_ptr()
+    return p
+
+
+def fpt_simulate(params: FptParams, n_traj: int, phi_in: float, phi_end: float, phi_uv: float,
+                 dN: float, bias: float, seed: int, out_N: torch.Tensor, out_logw: torch.Tensor):
+    _check(lib.fpt_simulate(ctypes.byref(params), n_traj, phi_in, phi_end, phi_uv, dN, bias, seed,
+                            _dptr(out_N, torch.float64), _dptr(out_logw, torch.float64)))
+
+
+def make_sets(specs: Sequence) -> ctypes.Array:
+    """fpt_set[] from objects with the fields of workloads.SetSpec."""
+    arr = (FptSet * len(specs))()
+    off = 0
+    for i, s in enumerate(specs):
+        a = arr[i]
+        a.phi_in, a.phi_end, a.phi_uv = s.phi_in, s.phi_end, s.phi_uv
+        a.m, a.b, a.dN, a.n_max = s.m, s.b, s.dN, s.n_max
+        a.n_traj = s.n_traj
+        a.traj_offset = getattr(s, "traj_offset", 0)
+        a.set_id = s.set_id
+        a.n_bins = s.n_bins
+        a.hist_lo, a.hist_hi = s.hist_lo, s.hist_hi
+        off += s.n_traj
+    return arr
+
+
+def fpt_simulate_batch(params: FptParams, sets: ctypes.Array, seed: int, out_N: torch.Tensor,
+                       out_logw: torch.Tensor, out_bins: Optional[torch.Tensor] = None,
+                       out_counts: Optional[torch.Tensor] = None):
+    _check(lib.fpt_simulate_batch(ctypes.byref(params), sets, len(sets), seed,
+                                  _dptr(out_N, torch.float64), _dptr(out_logw, torch.float64),
+                                  _dptr(out_bins), _dptr(out_counts)))
+
+
+def fpt_simulate_batch_host(params: FptParams, sets: ctypes.Array, seed: int, host_N, host_logw,
+                            host_bins, host_counts):
+    """Host buffers: torch CPU tensors (pinned or not), or None for N/logw."""
+    def hp(t):
+        if t is None:
+            return None
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    _check(lib.fpt_simulate_batch_host(ctypes.byref(params), sets, len(sets), seed, hp(host_N),
+                                       hp(host_logw), hp(host_bins), hp(host_counts)))
+
+
+def fpt_histogram(N: torch.Tensor, logw: torch.Tensor, n_bins: int, lo: float, hi: float,
+                  bins: torch.Tensor, counts: torch.Tensor, n_sub: int = 1, id_offset: int = 0,
+                  stream=None):
+    _check(lib.fpt_histogram(_dptr(N, torch.float64), _dptr(logw, torch.float64), N.numel(), n_bins,
+                             lo, hi, n_sub, id_offset, _dptr(bins), _dptr(counts), _stream(stream)))
+
+
+def fpt_normals(seed: int, traj: int, set_id: int, k0: int, n_blocks: int, precision, out: torch.Tensor,
+                stream=None):
+    prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    _check(lib.fpt_normals(seed, traj, set_id, k0, n_blocks, prec, _dptr(out), _stream(stream)))
+
+
+# ---- conveniences (allocation + unpacking; no arithmetic of the method) ----
+
+def empty_bins(n_bins: int, device="cuda") -> torch.Tensor:
+    return torch.empty((n_bins, BIN_FIELDS), dtype=torch.float64, device=device)
+
+
+def empty_counts(n: int = 1, device="cuda") -> torch.Tensor:
+    return torch.empty((n, 4), dtype=torch.int64, device=device)
+
+
+def bins_to_numpy(bins: torch.Tensor):
+    """(fields float64[n, 5], count int64[n]) from an fpt_bin array."""
+    b = bins.detach().cpu().contiguous()
+    f = b.numpy()[:, :5].copy()
+    c = b.view(torch.int64).numpy()[:, 5].copy()
+    return f, c
+
+
+def simulate_workload(workload, *, block_dim=0, k_steps=0, device="cuda", with_hist=True, stream=None,
+                      steps_out=None):
+    """Run all sets of a workloads.Workload in one batched call.  Returns
+    (N, logw, bins, counts) device tensors."""
+    specs = workload.sets
+    sets = make_sets(specs)
+    n = sum(s.n_traj for s in specs)
+    N = torch.empty(n, dtype=torch.float64, device=device)
+    lw = torch.empty(n, dtype=torch.float64, device=device)
+    bins = counts = None
+    if with_hist:
+        bins = empty_bins(sum(s.n_bins for s in specs), device)
+        counts = empty_counts(len(specs), device)
+    s0 = specs[0]
+    p = make_params(model=s0.model, precision=workload.precision, m=s0.m, a0=s0.a0, s0=s0.s0,
+                    n_max=s0.n_max, block_dim=block_dim, k_steps=k_steps, stream=stream,
+                    steps_out=steps_out)
+    fpt_simulate_batch(p, sets, workload.seed, N, lw, bins, counts)
+    return N, lw, bins, counts
