@@ -23,7 +23,10 @@
  * Conventions for every entry point:
  *   - All array arguments are DEVICE pointers owned by the caller unless the
  *     name ends in _host.  Outputs are indexed by trajectory, whatever order
- *     the GPU finishes them in, so results are deterministic.
+ *     the GPU finishes them in, so the records (N, ln w) are deterministic for
+ *     a given k_steps and independent of block_dim and of the grid.  Histogram
+ *     counts and maxima are exact; the FP64 bin sums are accumulated with
+ *     atomics, so their last bits can vary from call to call.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *     enqueued on it; the call then reads back a device status word, which
  *     synchronises that stream only.

@@ -125,7 +125,13 @@ def test_host_entry_matches_device_entry(nat):
     p = nat.make_params(precision=wl.precision, m=s0.m, n_max=s0.n_max)
     nat.fpt_simulate_batch_host(p, sets, wl.seed, hN, hl, hb, hc)
     assert torch.equal(hN, N.cpu()) and torch.equal(hl, lw.cpu())
-    assert torch.equal(hb, bins.cpu()) and torch.equal(hc, counts.cpu())
+    assert torch.equal(hc, counts.cpu())
+    # counts and maxima are exact; the FP64 sums are accumulated with atomics,
+    # so their last bits depend on the order the GPU happens to add them in
+    fb, cb = nat.bins_to_numpy(bins)
+    fh, ch = nat.bins_to_numpy(hb)
+    assert np.array_equal(cb, ch) and np.array_equal(fb[:, 0], fh[:, 0])
+    np.testing.assert_allclose(fh[:, 1:], fb[:, 1:], rtol=1e-12, atol=1e-12 * np.abs(fb[:, 3:]).max())
 
 
 def test_invalid_arguments_are_rejected_before_launch(nat):

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 * Philox words: bit-exact.  Normals: binary64 within a few ulp (CUDA's and
-  glibc's log/sin/cos differ by an ulp or two), binary32 within 2e-5.
+  glibc's log/sin/cos differ by an ulp or two); binary32 (hardware
+  approximations, 23-bit uniform) within ~1e-6 in the bulk.
 * FP64 stepper, per run: same crossing step for every run (n * 1e-6 < 1 at
   these sizes), |dN| <= 1e-12 N and |d ln w| <= 1e-12 max(1, sum_m |increment_m|).
 * Reduced precision: statistical parity (every histogram bin within 3 combined
@@ -88,7 +89,12 @@ def test_normals_match_oracle(nat):
     g64 = o64.cpu().numpy()
     g32 = o32.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(g64 - ref) / np.maximum(np.abs(ref), 1e-3)) < 4e-15
-    assert np.max(np.abs(g32 - ref)) < 2e-5
+    # binary32: the radius uses a 23-bit uniform, so |xi| > 3 deviates by up to
+    # ~1e-4 (|xi| cannot exceed sqrt(2 ln 2^24) = 5.77); the bulk tracks to ~1e-6
+    err = np.abs(g32 - ref)
+    assert np.median(err) < 1e-6
+    assert np.all(err < 2e-5 + 1e-4 * np.maximum(np.abs(ref) - 2.0, 0.0) ** 2)
+    assert np.all(np.abs(g32) < 5.78)
 
 
 CASES_F64 = [
@@ -110,12 +116,22 @@ def test_f64_per_run_parity(nat, case):
     assert_f64_parity(N_g, lw_g, N_o, lw_o, steps_o, case["b"], case["dN"])
 
 
-@pytest.mark.parametrize("block_dim,k_steps", [(32, 4), (64, 8), (512, 4)])
-def test_f64_parity_independent_of_launch_shape(nat, block_dim, k_steps):
+@pytest.mark.parametrize("precision,block_dim,k_steps", [("f64", 32, 4), ("f64", 512, 4),
+                                                         ("f64", 64, 8), ("f32_kahan", 64, 8),
+                                                         ("f32_f64acc", 512, 32)])
+def test_results_independent_of_launch_shape(nat, precision, block_dim, k_steps):
+    """Records do not depend on the block size; the block length k_steps only
+    changes how the normals' running sum is associated (last bits of ln w in
+    binary64; binary32 block sums are rounded per block)."""
     case = dict(n=2049, phi_in=3.0, dN=1e-3, b=1.0, n_max=6.0)
-    N_g, lw_g, _ = gpu_run(nat, precision="f64", block_dim=block_dim, k_steps=k_steps, **case)
-    N_ref, lw_ref, _ = gpu_run(nat, precision="f64", **case)
+    N_g, lw_g, _ = gpu_run(nat, precision=precision, block_dim=block_dim, k_steps=k_steps, **case)
+    ks_default = 4 if precision == "f64" else 16
+    N_ref, lw_ref, _ = gpu_run(nat, precision=precision, k_steps=k_steps, **case)
     assert np.array_equal(N_g, N_ref) and np.array_equal(lw_g, lw_ref)
+    N_d, lw_d, _ = gpu_run(nat, precision=precision, k_steps=ks_default, **case)
+    assert np.array_equal(N_g, N_d)
+    tol = 1e-12 if precision == "f64" else 1e-4
+    assert np.max(np.abs(lw_g - lw_d)) < tol * max(1.0, np.abs(lw_d).max())
 
 
 def test_degenerate_inputs(nat):
@@ -191,4 +207,9 @@ def test_f32_drift_dominated_matches_f64_gpu(nat, precision):
         assert np.all(np.isfinite(N32)) and np.all(np.isfinite(N64))
         assert abs(N32.mean() / N64.mean() - 1) < 1e-4
         assert np.max(np.abs(N32 - N64)) < 0.02 * 0.0203  # a few percent of sigma_N
-        assert np.max(np.abs(lw32 - lw64)) < 1e-2 * max(1.0, b)
+        # per-run log-weight error: tiny unless the binary32 run crosses one step
+        # earlier or later (then ln w moves by one step's increment)
+        dl = np.abs(lw32 - lw64)
+        assert np.median(dl) < 1e-4 * max(1.0, b)
+        assert np.mean(dl > 1e-3 * max(1.0, b)) < 0.01
+        assert np.max(dl) < 1.5 * b * math.sqrt(1e-3) * 6 + 1e-3
