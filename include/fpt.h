@@ -166,6 +166,29 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
                             double* host_N, double* host_logw, fpt_bin* host_bins,
                             fpt_hist_counts* host_counts);
 
+/* No-allocation variant of fpt_simulate_batch (records only, no histograms).
+ * The paper has no counterpart: this entry exists for callers that must not
+ * allocate device memory while they run — for example a process whose device
+ * memory is entirely reserved by its own pool allocator or a fixed budget, or a
+ * latency-bound loop that cannot afford an allocation failing mid-run or the
+ * device synchronisation that freeing memory implies.  The caller passes the
+ * inputs (host sets array) and the device outputs exactly as for
+ * fpt_simulate_batch; the stepper's scratch (ticket counter, step total, status
+ * word and up to FPT_NOALLOC_MAX_SETS per-set constant blocks, under 8 KB) is a
+ * fixed array inside the library that every GPU loading the library keeps
+ * until the process exits.  No device memory is allocated or freed.
+ *   - n_sets must be in [1, FPT_NOALLOC_MAX_SETS]; more is rejected with
+ *     FPT_EINVAL (fpt_last_error() says why).
+ *   - The first call on a device looks up the array's device address for that
+ *     device (and caches it); make that first call before any stream capture.
+ *   - All calls share the one array: each call re-initialises what it uses,
+ *     but calls whose GPU work overlaps (other streams or host threads) race
+ *     on it and must be serialised by the caller.
+ *   - Results equal those of fpt_simulate_batch with the same arguments. */
+#define FPT_NOALLOC_MAX_SETS 48
+int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* sets, int32_t n_sets,
+                               uint64_t seed, double* out_N, double* out_logw);
+
 /* Diagnostic: the unit normals xi_{4k} .. xi_{4k+3} for k = k0 .. k0 + n_blocks - 1
  * of run `traj` of set `set_id` (exactly what the stepper draws; §2.1 below
  * Eq. (8)), written to the device array out as double (FPT_PREC_F64) or float

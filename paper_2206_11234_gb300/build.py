@@ -26,6 +26,7 @@ UNITS = {
     "stepper_f32.cu": [],
     "stepper_f64.cu": ["-fmad=false"],
     "rng_probe.cu": ["-fmad=false"],
+    "noalloc.cu": [],
 }
 
 
