@@ -89,12 +89,16 @@ def test_normals_match_oracle(nat):
     g64 = o64.cpu().numpy()
     g32 = o32.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(g64 - ref) / np.maximum(np.abs(ref), 1e-3)) < 4e-15
-    # binary32: the radius uses a 23-bit uniform, so |xi| > 3 deviates by up to
-    # ~1e-4 (|xi| cannot exceed sqrt(2 ln 2^24) = 5.77); the bulk tracks to ~1e-6
+    # binary32 error budget per normal, from the pair radius r = sqrt(xi0^2 + xi1^2):
+    # the 23-bit uniform moves -2 ln u0 by <= 2^-23 e^{r^2/2}, lg2.approx by <= 2^-22 ln 4,
+    # both divided by 2r in r; the angle (quantised u1, binary32 2 pi, sin/cos.approx)
+    # is good to ~1.5e-6 rad
+    r = np.repeat(np.hypot(ref[0::2], ref[1::2]), 2)
+    bound = (2.0**-23 * np.exp(r * r / 2) + 2.0**-22 * 1.3863) / (2 * r) + 1.5e-6 * r + 1e-6
     err = np.abs(g32 - ref)
+    assert np.all(err < 2 * bound), np.max(err / bound)
     assert np.median(err) < 1e-6
-    assert np.all(err < 2e-5 + 1e-4 * np.maximum(np.abs(ref) - 2.0, 0.0) ** 2)
-    assert np.all(np.abs(g32) < 5.78)
+    assert np.all(np.abs(g32) < 5.78)  # largest binary32 radius: sqrt(2 ln 2^24)
 
 
 CASES_F64 = [
@@ -209,7 +213,17 @@ def test_f32_drift_dominated_matches_f64_gpu(nat, precision):
         assert np.max(np.abs(N32 - N64)) < 0.02 * 0.0203  # a few percent of sigma_N
         # per-run log-weight error: tiny unless the binary32 run crosses one step
         # earlier or later (then ln w moves by one step's increment)
+        # (binary32 phi drifts ~2e-5 from binary64 over ~8600 steps, against a last
+        # step of ~1.4e-3, so a few percent of runs flip)
         dl = np.abs(lw32 - lw64)
+        flip = dl > 1e-3 * max(1.0, b)
         assert np.median(dl) < 1e-4 * max(1.0, b)
-        assert np.mean(dl > 1e-3 * max(1.0, b)) < 0.01
+        assert np.mean(flip) < 0.05
         assert np.max(dl) < 1.5 * b * math.sqrt(1e-3) * 6 + 1e-3
+        # statistically the two precisions agree bin by bin (400 bins on (7, 10])
+        b32, _ = oracle.histogram(N32, lw32, 400, 7.0, 10.0)
+        b64, _ = oracle.histogram(N64, lw64, 400, 7.0, 10.0)
+        P32, s32 = _pdf_and_sigma(b32[0], N32.size, 7.0, 10.0)
+        P64, s64 = _pdf_and_sigma(b64[0], N64.size, 7.0, 10.0)
+        sig = np.hypot(s32, s64)
+        assert np.all((np.abs(P32 - P64) <= 3 * sig) | ((sig == 0) & (P32 == P64)))
