@@ -238,6 +238,11 @@ def main():
                                n_max=s0.n_max, block_dim=args.block_dim, k_steps=args.k_steps,
                                stream=stream, steps_out=steps_out)
 
+    # launch shape from the library's autotuner (pilot on 2 % of the workload; untimed setup)
+    tuned = None
+    if args.block_dim == 0 and args.k_steps == 0:
+        tb, tk, trate = nat.fpt_autotune(params(wl.precision), sets, seed=99, fraction=0.02)
+        tuned = {"block_dim": tb, "k_steps": tk, "pilot_steps_per_s": trate}
     p = params(wl.precision, steps_ctr)
 
     def one_step(seed):
@@ -366,7 +371,8 @@ def main():
     roof = {"bound": "alu", "achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9,
             "peak": issue_peak / 1e9, "unit": "Gwarp-inst/s (algorithmic)",
             "frac": achieved_steps / steps_peak, "traffic": None,
-            "kernel": "stepper_kernel<float, F32_KAHAN, QUADRATIC, no wall, 16>",
+            "kernel": f"stepper_kernel<float, {wl.precision}, quadratic, "
+                      f"k_steps {(tuned or {}).get('k_steps', args.k_steps)}>",
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
             "peak_source": f"{n_sm} SMs x 4 issue/clk x {f_max / 1e6:.0f} MHz (max SM clock, "
                            "MEASURED_PEAKS.json); MUFU co-bound 16/clk/SM"}
@@ -381,7 +387,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl.name, "precision": wl.precision, "runs_per_gpu": n,
                    "sets": len(specs), "l2": "outputs (16 B/run) exceed L2; no inputs besides parameters",
-                   "parallelism": f"dp{world} (disjoint run ids per GPU)"},
+                   "parallelism": f"dp{world} (disjoint run ids per GPU)",
+                   "launch_shape": tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
         "roofline": roof,

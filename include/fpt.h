@@ -158,6 +158,21 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
 
+/* Autotuner of the stepper's launch shape (threads per block in {128, 256, 512}
+ * and steps per scheduling block k_steps in {8, 16, 32}, binary64: {4, 8}).
+ * Runs pilot launches over the given sets with each n_traj scaled by
+ * `fraction` in (0, 1] (raised if needed so the pilot fills the GPU), times
+ * each shape with CUDA events on p->stream and keeps the fastest in EM steps
+ * per second.  The result is cached per (device, precision, model, wall) and
+ * used by every later call whose block_dim or k_steps is 0.  Outputs (host,
+ * each may be NULL): the chosen shape and its pilot steps/s.  Records do not
+ * depend on block_dim; k_steps only changes the rounding of the ln w sum. */
+int fpt_autotune(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
+                 double fraction, int32_t* block_dim_out, int32_t* k_steps_out,
+                 double* steps_per_s_out);
+/* Forget every autotuned shape (later calls use the defaults until re-tuned). */
+void fpt_autotune_reset(void);
+
 /* End-to-end call with HOST buffers: copies nothing in but the parameters,
  * runs fpt_simulate_batch with bins on a private device workspace and copies
  * (N, ln w) and the histograms back to host_N/host_logw (may be NULL to skip)

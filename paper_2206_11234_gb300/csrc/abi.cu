@@ -172,8 +172,16 @@ int prepare(const fpt_params* p, const fpt_set* sets, int n_sets, bool with_hist
 }
 
 int pick_stepper(const fpt_params* p, bool wall, StepperKernel* k, int* block) {
-    const int b = p->block_dim ? p->block_dim : 256;
+    int b = p->block_dim;
     int s = p->k_steps;
+    if (b == 0 || s == 0) {
+        int tb = 0, ts = 0;
+        if (tuned_shape(p->precision, p->model, wall, &tb, &ts)) {
+            if (b == 0) b = tb;
+            if (s == 0) s = ts;
+        }
+    }
+    if (b == 0) b = 256;
     if (p->precision == FPT_PREC_F64) {
         if (s == 0) s = 4;
         *k = stepper_f64(p->model, wall, s);
@@ -186,12 +194,15 @@ int pick_stepper(const fpt_params* p, bool wall, StepperKernel* k, int* block) {
     return FPT_OK;
 }
 
-int stepper_grid(const StepperKernel& k, int block, unsigned long long n_total, int* grid) {
+int stepper_grid(const StepperKernel& k, int block, int n_sets, unsigned long long n_total, int* grid) {
     int n_sm = 0;
     int rc = device_sm_count(&n_sm);
     if (rc) return rc;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, block, 0);
+    const size_t smem = stepper_smem(k, block, n_sets);
+    cudaError_t e = cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "stepper shared memory");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, block, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) per_sm = 1;
     const unsigned long long full = (unsigned long long)per_sm * n_sm;
@@ -224,14 +235,13 @@ int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L
     int block = 0, grid = 0;
     int rc = pick_stepper(p, P.wall, &k, &block);
     if (rc) return rc;
-    rc = stepper_grid(k, block, P.n_total, &grid);
+    rc = stepper_grid(k, block, (int)P.sets.size(), P.n_total, &grid);
     if (rc) return rc;
-    StepperArgs a;
+    StepperParams a;
+    a.keys = philox_keys(seed);
     a.sets = reinterpret_cast<const SetConst*>(ws + L.off_sets);
     a.n_sets = (int)P.sets.size();
     a.n_total = P.n_total;
-    a.key0 = (uint32_t)seed;
-    a.key1 = (uint32_t)(seed >> 32);
     a.out_N = out_N;
     a.out_logw = out_logw;
     a.scratch = reinterpret_cast<StepperScratch*>(ws + L.off_scratch);

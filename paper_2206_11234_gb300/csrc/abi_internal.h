@@ -34,7 +34,10 @@ struct WorkspaceLayout {
 int prepare(const fpt_params* p, const fpt_set* sets, int n_sets, bool with_hist, Prepared* P);
 int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetConst* out);
 int pick_stepper(const fpt_params* p, bool wall, StepperKernel* k, int* block);
-int stepper_grid(const StepperKernel& k, int block, unsigned long long n_total, int* grid);
+// Launch shape chosen by fpt_autotune for this device and kind of launch, if any.
+bool tuned_shape(int precision, int model, bool wall, int* block, int* ks);
+void clear_tuned_shapes();
+int stepper_grid(const StepperKernel& k, int block, int n_sets, unsigned long long n_total, int* grid);
 void workspace_layout(const Prepared& P, WorkspaceLayout* L);
 void workspace_image(const Prepared& P, const WorkspaceLayout& L, std::vector<unsigned char>* img);
 int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L, unsigned char* ws,

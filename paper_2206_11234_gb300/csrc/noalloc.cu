@@ -90,7 +90,7 @@ extern "C" int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* se
     int block = 0, grid = 0;
     rc = pick_stepper(p, wall, &k, &block);
     if (rc) return rc;
-    rc = stepper_grid(k, block, n_total, &grid);
+    rc = stepper_grid(k, block, n_sets, n_total, &grid);
     if (rc) return rc;
     unsigned char* ws = nullptr;
     rc = scratch_address(&ws);
@@ -102,12 +102,11 @@ extern "C" int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* se
     cudaError_t e = cudaMemcpyAsync(ws, img, bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "no-alloc scratch upload");
 
-    StepperArgs a;
+    StepperParams a;
+    a.keys = philox_keys(seed);
     a.sets = reinterpret_cast<const SetConst*>(ws + kScratchHeader);
     a.n_sets = n_sets;
     a.n_total = n_total;
-    a.key0 = (uint32_t)seed;
-    a.key1 = (uint32_t)(seed >> 32);
     a.out_N = out_N;
     a.out_logw = out_logw;
     a.scratch = reinterpret_cast<StepperScratch*>(ws);

@@ -16,6 +16,23 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
+// Round keys of Philox4x32-10 for one seed: key r = (seed_lo + r W0, seed_hi + r W1).
+// Computed once on the host and passed by value as a kernel parameter, so each
+// round XORs a constant-bank operand instead of recomputing its key.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys k;
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = (uint32_t)seed + (uint32_t)r * kPhiloxW0;
+        k.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * kPhiloxW1;
+    }
+    return k;
+}
+
 // Per-trajectory part of Philox round 1.  Round 1 multiplies counter word 2
 // (id_hi) and XORs word 1 (id_lo) and word 3 (set_id): those do not change
 // along a trajectory, so they are folded once at refill.
@@ -25,13 +42,12 @@ struct PhiloxLane {
     uint32_t r1_set; // set_id ^ key1
 };
 
-__device__ __forceinline__ PhiloxLane philox_lane(uint64_t id, uint32_t set_id, uint32_t key0,
-                                                  uint32_t key1) {
+__device__ __forceinline__ PhiloxLane philox_lane(uint64_t id, uint32_t set_id, const PhiloxKeys& K) {
     const uint64_t p = (uint64_t)kPhiloxM1 * (uint32_t)(id >> 32);
     PhiloxLane l;
-    l.r1_x0 = (uint32_t)(p >> 32) ^ (uint32_t)id ^ key0;
+    l.r1_x0 = (uint32_t)(p >> 32) ^ (uint32_t)id ^ K.k0[0];
     l.r1_x1 = (uint32_t)p;
-    l.r1_set = set_id ^ key1;
+    l.r1_set = set_id ^ K.k1[0];
     return l;
 }
 
@@ -48,17 +64,16 @@ __device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_
 }
 
 // Philox4x32-10 of counter (k, id_lo, id_hi, set_id): round 1 from the lane's
-// folded words, rounds 2..10 with the bumped keys.
-__device__ __forceinline__ void philox_block(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                             uint32_t key1, uint32_t w[4]) {
+// folded words, rounds 2..10 with the precomputed keys.
+__device__ __forceinline__ void philox_block(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
+                                             uint32_t w[4]) {
     const uint64_t p0 = (uint64_t)kPhiloxM0 * k;
     uint32_t x0 = l.r1_x0;
     uint32_t x1 = l.r1_x1;
     uint32_t x2 = (uint32_t)(p0 >> 32) ^ l.r1_set;
     uint32_t x3 = (uint32_t)p0;
 #pragma unroll
-    for (int r = 1; r < 10; ++r)
-        philox_round(x0, x1, x2, x3, key0 + (uint32_t)r * kPhiloxW0, key1 + (uint32_t)r * kPhiloxW1);
+    for (int r = 1; r < 10; ++r) philox_round(x0, x1, x2, x3, K.k0[r], K.k1[r]);
     w[0] = x0;
     w[1] = x1;
     w[2] = x2;
@@ -92,22 +107,23 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double&
     z1 = r * s;
 }
 
-__device__ __forceinline__ void normals4_f64(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                             uint32_t key1, double xi[4]) {
+__device__ __forceinline__ void normals4_f64(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
+                                             double xi[4]) {
     uint32_t w[4];
-    philox_block(l, k, key0, key1, w);
+    philox_block(l, k, K, w);
     box_muller_f64(w[0], w[1], xi[0], xi[1]);
     box_muller_f64(w[2], w[3], xi[2], xi[3]);
 }
 
 // ---- Box–Muller, binary32 (hardware approximations) ----
-// u = ((w >> 9) + 1/2) 2^-23 is exact in binary32: OR the 23 bits into the
-// mantissa of 1.0 and subtract 1 - 2^-24 (exact by Sterbenz).  The angle is
+// u = ((w >> 9) + 1/2) 2^-23 is exact in binary32: put the top 23 bits into
+// the mantissa of 1.0 (a shift-add, the bits do not overlap) and subtract
+// 1 - 2^-24 (exact by Sterbenz).  The angle is
 // taken as 2 pi u - pi in [-pi, pi), where the fast sine/cosine are accurate;
 // sin(2 pi u - pi) = -sin(2 pi u) and likewise for cos, so the sign is folded
 // into r.  The result tracks the binary64 normals to ~1e-6.
 __device__ __forceinline__ float uniform_f32(uint32_t w) {
-    return __int_as_float(0x3f800000u | (w >> 9)) - (1.0f - 0x1p-24f);
+    return __int_as_float((w >> 9) + 0x3f800000u) - (1.0f - 0x1p-24f);
 }
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -128,10 +144,10 @@ __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& 
     z1 = neg_r * s;
 }
 
-__device__ __forceinline__ void normals4_f32(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                             uint32_t key1, float xi[4]) {
+__device__ __forceinline__ void normals4_f32(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
+                                             float xi[4]) {
     uint32_t w[4];
-    philox_block(l, k, key0, key1, w);
+    philox_block(l, k, K, w);
     box_muller_f32(w[0], w[1], xi[0], xi[1]);
     box_muller_f32(w[2], w[3], xi[2], xi[3]);
 }

@@ -6,12 +6,15 @@
 // §2.2 Eq. (11) followed by the reflecting wall, and the lane keeps the
 // minimum phi of the block.  At the block end a lane whose minimum reached
 // phi_end (first passage, §2.1 below Eq. (8)) or whose step count reached the
-// censoring cap replays the block from its saved start state with a per-step
-// test — bit-identical arithmetic, the same Philox counters — to find the
-// exact step, interpolates the crossing time in binary64 and writes its
-// record.  Finished lanes then refill from a global ticket counter (one
-// atomicAdd per warp), so a warp keeps 32 live runs whatever their lengths
-// (persistent scheduler).
+// censoring cap has finished somewhere inside the block: it pushes its
+// block-start state onto its warp's replay queue in shared memory and refills
+// at once from a global ticket counter (one atomicAdd per warp), so a warp
+// keeps 32 live runs whatever their lengths (persistent scheduler).  When 32
+// finished runs are queued, the warp replays their blocks together, step by
+// step with a test after each step — bit-identical arithmetic, the same
+// Philox counters — to find the exact step, interpolates the crossing time in
+// binary64 and writes the records.  Replays thus run with all 32 lanes busy
+// instead of stalling a warp once per finished run.
 //
 // Log-weight (§2.2 Eqs. (12)-(14), sign as derived from Eqs. (13)-(14)):
 // with B = b S the step term is -(b xi sqrt(dN) + b^2 dN / 2), so a run of M
@@ -146,17 +149,16 @@ struct WSum<FPT_PREC_F64> {
 };
 
 template <typename Real>
-__device__ __forceinline__ void normals4(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                         uint32_t key1, Real xi[4]);
+__device__ __forceinline__ void normals4(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K, Real xi[4]);
 template <>
-__device__ __forceinline__ void normals4<float>(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                                uint32_t key1, float xi[4]) {
-    normals4_f32(l, k, key0, key1, xi);
+__device__ __forceinline__ void normals4<float>(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
+                                                float xi[4]) {
+    normals4_f32(l, k, K, xi);
 }
 template <>
-__device__ __forceinline__ void normals4<double>(const PhiloxLane& l, uint32_t k, uint32_t key0,
-                                                 uint32_t key1, double xi[4]) {
-    normals4_f64(l, k, key0, key1, xi);
+__device__ __forceinline__ void normals4<double>(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
+                                                 double xi[4]) {
+    normals4_f64(l, k, K, xi);
 }
 
 template <typename Real>
@@ -166,31 +168,157 @@ __device__ __forceinline__ float real_min<float>(float a, float b) { return fmin
 template <>
 __device__ __forceinline__ double real_min<double>(double a, double b) { return fmin(a, b); }
 
+template <typename Real>
+__device__ __forceinline__ Real set_phi_in(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_phi_in : (Real)S.phi_in; }
+template <typename Real>
+__device__ __forceinline__ Real set_phi_end(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_phi_end : (Real)S.phi_end; }
+template <typename Real>
+__device__ __forceinline__ Real set_twouv(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_twouv : (Real)S.twouv; }
+
+// A run that finished inside its last block, waiting for the replay.
+template <typename Real, int PREC>
+struct Pending {
+    unsigned long long rec;  // record index
+    int m0;                  // step count at the block start
+    int set;                 // parameter set
+    Real phi0;               // phi at the block start
+    WSum<PREC> W;            // running sum of the normals before the block
+};
+
+constexpr int kQueueCap = 64;  // per warp: up to 31 waiting + 32 new
+constexpr int kParkWords = 12;  // per thread: a run's live state during a batch replay
+
+// Park / unpark 32-bit words through volatile shared memory, so the values are
+// really dead in registers while the replay runs (no store-to-load forwarding).
+__device__ __forceinline__ void park(volatile unsigned* v, int i, unsigned x) { v[i] = x; }
+__device__ __forceinline__ unsigned unpark(volatile unsigned* v, int i) { return v[i]; }
+__device__ __forceinline__ void park_f(volatile unsigned* v, int i, float x) { v[i] = __float_as_uint(x); }
+__device__ __forceinline__ float unpark_f(volatile unsigned* v, int i) { return __uint_as_float(v[i]); }
+__device__ __forceinline__ void park_d(volatile unsigned* v, int i, double x) {
+    v[i] = (unsigned)__double2loint(x);
+    v[i + 1] = (unsigned)__double2hiint(x);
+}
+__device__ __forceinline__ double unpark_d(volatile unsigned* v, int i) {
+    return __hiloint2double((int)v[i + 1], (int)v[i]);
+}
+template <typename Real>
+__device__ __forceinline__ void park_r(volatile unsigned* v, int i, Real x) {
+    if constexpr (sizeof(Real) == 4) park_f(v, i, (float)x); else park_d(v, i, (double)x);
+}
+template <typename Real>
+__device__ __forceinline__ Real unpark_r(volatile unsigned* v, int i) {
+    if constexpr (sizeof(Real) == 4) return (Real)unpark_f(v, i); else return (Real)unpark_d(v, i);
+}
+template <int PREC>
+__device__ __forceinline__ void park_w(volatile unsigned* v, int i, const WSum<PREC>& W) {
+    if constexpr (PREC == FPT_PREC_F32_KAHAN) { park_f(v, i, W.s); park_f(v, i + 1, W.c); }
+    else park_d(v, i, W.s);
+}
+template <int PREC>
+__device__ __forceinline__ void unpark_w(volatile unsigned* v, int i, WSum<PREC>& W) {
+    if constexpr (PREC == FPT_PREC_F32_KAHAN) { W.s = unpark_f(v, i); W.c = unpark_f(v, i + 1); }
+    else W.s = unpark_d(v, i);
+}
+
+// dynamic shared memory per warp: the replay queue plus the parking slots
+template <typename Real, int PREC>
+constexpr int warp_smem_bytes() { return kQueueCap * (int)sizeof(Pending<Real, PREC>) + 32 * kParkWords * 4; }
+
+// Replay the blocks of cnt queued runs (lane j takes entry j), find each run's
+// first passage or cap step and write its record.  Called by a whole warp, once
+// per 32 finished runs, while the lanes' own runs are parked in shared memory.
+template <typename Real, int PREC, int MODEL, bool WALL, int KS>
+__device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int cnt, const StepperParams& P,
+                                             const SetConst* s_sets, unsigned lane,
+                                             unsigned long long& my_steps) {
+    const unsigned mask = cnt >= 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    if ((int)lane >= cnt) return;
+    const Pending<Real, PREC> e = q[lane];
+    const SetConst& S = s_sets[e.set];
+    ModelStep<Real, MODEL> model;
+    model.load(S);
+    const Real phi_end = set_phi_end<Real>(S);
+    const Real twouv = set_twouv<Real>(S);
+    const PhiloxLane pl = philox_lane(S.traj_offset + (e.rec - (unsigned long long)S.first), S.set_id, P.keys);
+    Real ph = e.phi0, prev = e.phi0, s2 = (Real)0;
+    int M = 0;
+    bool crossed = false;
+    const uint32_t k0 = (uint32_t)e.m0 >> 2;
+    for (int g = 0; g < KS / 4; ++g) {
+        Real xi[4];
+        normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            if (M == 0) {
+                prev = ph;
+                ph = model.step(ph, xi[q4]);
+                if constexpr (WALL) ph = real_min<Real>(ph, twouv - ph);
+                s2 += xi[q4];
+                const int step_index = e.m0 + 4 * g + q4;
+                if (ph <= phi_end) {
+                    crossed = true;
+                    M = step_index + 1;
+                } else if (step_index + 1 >= S.m_max) {
+                    M = step_index + 1;
+                }
+            }
+        }
+        if (__all_sync(mask, M != 0)) break;
+    }
+    const double Wtot = e.W.total(s2);
+    double N;
+    if (crossed) {
+        // linear interpolation of the crossing inside step M-1, in binary64
+        const double a = (double)prev, c = (double)ph, pe = (double)phi_end;
+        const double theta = (a - pe) / (a - c);
+        N = ((double)(M - 1) + theta) * S.dN;
+    } else {
+        N = __longlong_as_double(0x7ff0000000000000ll);  // +inf: censored
+    }
+    P.out_N[e.rec] = N;
+    P.out_logw[e.rec] = -S.lw_bsq * Wtot - S.lw_half_b2dN * (double)M;
+    my_steps += (unsigned long long)M;
+}
+
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
+// Register cap per thread.  48 keeps the binary32 hot loop spill-free at 40
+// resident warps per SM (5 blocks of 256); the binary64 reference kernels are
+// built with a larger cap.
+#ifndef FPT_STEPPER_MAXNREG
+#define FPT_STEPPER_MAXNREG 48
+#endif
 template <typename Real, int PREC, int MODEL, bool WALL, int KS>
-__global__ void __launch_bounds__(kStepperMaxThreads)
-stepper_kernel(const SetConst* __restrict__ sets, int n_sets, uint64_t n_total, uint32_t key0,
-               uint32_t key1, double* __restrict__ out_N, double* __restrict__ out_logw,
-               StepperScratch* __restrict__ scratch, unsigned long long* __restrict__ steps_out) {
+__global__ void __maxnreg__(FPT_STEPPER_MAXNREG)
+stepper_kernel(const StepperParams P) {
     static_assert(KS % 4 == 0, "a scheduling block is a whole number of Philox blocks");
-    __shared__ SetConst s_sets[FPT_MAX_SETS];
-    __shared__ long long s_first[FPT_MAX_SETS + 1];
+    using Entry = Pending<Real, PREC>;
+    // dynamic shared memory: [set table][set starts][per-warp replay queues][parking slots]
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const int n_sets = P.n_sets;
+    SetConst* s_sets = reinterpret_cast<SetConst*>(s_dyn);
+    long long* s_first = reinterpret_cast<long long*>(s_dyn + (size_t)n_sets * sizeof(SetConst));
+    unsigned char* s_queue = s_dyn + stepper_table_bytes(n_sets);
+    Entry* q = reinterpret_cast<Entry*>(s_queue) + (threadIdx.x >> 5) * kQueueCap;
+    // parking slots follow the queues: kParkWords words per thread, interleaved by thread
+    volatile unsigned* park_slot = reinterpret_cast<volatile unsigned*>(
+        s_queue + (size_t)(blockDim.x >> 5) * kQueueCap * sizeof(Entry)) + threadIdx.x;
     for (int i = threadIdx.x; i < n_sets; i += blockDim.x) {
-        s_sets[i] = sets[i];
-        s_first[i] = sets[i].first;
+        s_sets[i] = P.sets[i];
+        s_first[i] = P.sets[i].first;
     }
-    if (threadIdx.x == 0) s_first[n_sets] = (long long)n_total;
+    if (threadIdx.x == 0) s_first[n_sets] = (long long)P.n_total;
     __syncthreads();
 
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     // lane state
     bool live = false, exhausted = false;
     int set = 0;
-    uint64_t rec = 0;  // record index (= ticket)
+    unsigned long long rec = 0;  // record index (= ticket)
     Real phi = (Real)0, phi_end = (Real)0, twouv = (Real)0;
     int m = 0, m_max = 0;
     PhiloxLane pl{0u, 0u, 0u};
@@ -199,6 +327,7 @@ stepper_kernel(const SetConst* __restrict__ sets, int n_sets, uint64_t n_total, 
     WSum<PREC> W;
     W.reset();
     unsigned long long my_steps = 0;
+    int q_count = 0;  // warp-uniform
 
     for (;;) {
         // ---- refill: lanes without a run take tickets (one atomic per warp) ----
@@ -208,11 +337,11 @@ stepper_kernel(const SetConst* __restrict__ sets, int n_sets, uint64_t n_total, 
             if (need == 0u) break;
             const int leader = __ffs(need) - 1;
             unsigned long long base = 0;
-            if ((int)lane == leader) base = atomicAdd(&scratch->ticket, (unsigned long long)__popc(need));
+            if ((int)lane == leader) base = atomicAdd(&P.scratch->ticket, (unsigned long long)__popc(need));
             base = __shfl_sync(FULL, base, leader);
             if (want) {
-                const uint64_t t = base + (uint64_t)__popc(need & ((1u << lane) - 1u));
-                if (t >= n_total) {
+                const unsigned long long t = base + (unsigned long long)__popc(need & lt_mask);
+                if (t >= P.n_total) {
                     exhausted = true;
                 } else {
                     // set of record t: the last s with first[s] <= t
@@ -224,25 +353,18 @@ stepper_kernel(const SetConst* __restrict__ sets, int n_sets, uint64_t n_total, 
                     set = lo;
                     const SetConst& S = s_sets[set];
                     rec = t;
-                    const uint64_t id = S.traj_offset + (t - (uint64_t)S.first);
-                    pl = philox_lane(id, S.set_id, key0, key1);
+                    pl = philox_lane(S.traj_offset + (t - (unsigned long long)S.first), S.set_id, P.keys);
                     model.load(S);
-                    if constexpr (sizeof(Real) == 4) {
-                        phi = S.f_phi_in;
-                        phi_end = S.f_phi_end;
-                        twouv = S.f_twouv;
-                    } else {
-                        phi = S.phi_in;
-                        phi_end = S.phi_end;
-                        twouv = S.twouv;
-                    }
+                    phi = set_phi_in<Real>(S);
+                    phi_end = set_phi_end<Real>(S);
+                    twouv = set_twouv<Real>(S);
                     m = 0;
                     m_max = S.m_max;
                     W.reset();
                     if (S.phi_in <= S.phi_end) {
                         // starts at or below the end of inflation: N = 0, w = 1
-                        out_N[t] = 0.0;
-                        out_logw[t] = 0.0;
+                        P.out_N[t] = 0.0;
+                        P.out_logw[t] = 0.0;
                     } else {
                         live = true;
                     }
@@ -260,70 +382,87 @@ stepper_kernel(const SetConst* __restrict__ sets, int n_sets, uint64_t n_total, 
 #pragma unroll
         for (int g = 0; g < KS / 4; ++g) {
             Real xi[4];
-            normals4<Real>(pl, k0 + (uint32_t)g, key0, key1, xi);
+            normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                phi = model.step(phi, xi[q]);
+            for (int q4 = 0; q4 < 4; ++q4) {
+                phi = model.step(phi, xi[q4]);
                 if constexpr (WALL) phi = real_min<Real>(phi, twouv - phi);  // mirror at phi_uv
                 mn = real_min<Real>(mn, phi);
-                sblk += xi[q];
+                sblk += xi[q4];
             }
         }
         m = m0 + KS;
         const bool event = live && (mn <= phi_end || m >= m_max);
-
-        if (__any_sync(FULL, event)) {
+        const unsigned ev = __ballot_sync(FULL, event);
+        if (ev) {
+            // finished inside this block: queue the block-start state, free the lane
             if (event) {
-                // replay the block step by step to find the first passage or the cap
-                Real ph = phi0, prev = phi0, s2 = (Real)0;
-                int M = 0;
-                bool crossed = false;
-                for (int g = 0; g < KS / 4 && M == 0; ++g) {
-                    Real xi[4];
-                    normals4<Real>(pl, k0 + (uint32_t)g, key0, key1, xi);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (M == 0) {
-                            prev = ph;
-                            ph = model.step(ph, xi[q]);
-                            if constexpr (WALL) ph = real_min<Real>(ph, twouv - ph);
-                            s2 += xi[q];
-                            const int step_index = m0 + 4 * g + q;
-                            if (ph <= phi_end) {
-                                crossed = true;
-                                M = step_index + 1;
-                            } else if (step_index + 1 >= m_max) {
-                                M = step_index + 1;
-                            }
-                        }
-                    }
-                }
-                const SetConst& S = s_sets[set];
-                const double Wtot = W.total(s2);
-                double N;
-                if (crossed) {
-                    // linear interpolation of the crossing inside step M-1, in binary64
-                    const double a = (double)prev, c = (double)ph, e = (double)phi_end;
-                    const double theta = (a - e) / (a - c);
-                    N = ((double)(M - 1) + theta) * S.dN;
-                } else {
-                    N = __longlong_as_double(0x7ff0000000000000ll);  // +inf: censored
-                }
-                out_N[rec] = N;
-                out_logw[rec] = -S.lw_bsq * Wtot - S.lw_half_b2dN * (double)M;
-                my_steps += (unsigned long long)M;
+                Entry& slot = q[q_count + __popc(ev & lt_mask)];
+                slot.rec = rec;
+                slot.m0 = m0;
+                slot.set = set;
+                slot.phi0 = phi0;
+                slot.W = W;
                 live = false;
+            }
+            q_count += __popc(ev);
+            if (q_count >= 32) {
+                // park this lane's run (the stride keeps one thread's words in one bank)
+                const unsigned stride = blockDim.x;
+                volatile unsigned* v = park_slot;
+                park_r<Real>(v, 0 * stride, phi);
+                park_w<PREC>(v, 2 * stride, W);  // 2 words
+                park(v, 4 * stride, (unsigned)m);
+                park(v, 5 * stride, (unsigned)rec);
+                park(v, 6 * stride, (unsigned)(rec >> 32));
+                park(v, 7 * stride, (unsigned)set | (live ? 0x40000000u : 0u) | (exhausted ? 0x80000000u : 0u));
+                park(v, 8 * stride, pl.r1_x0);
+                park(v, 9 * stride, pl.r1_x1);
+                park(v, 10 * stride, pl.r1_set);
+                __syncwarp();
+                replay_batch<Real, PREC, MODEL, WALL, KS>(q, 32, P, s_sets, lane, my_steps);
+                __syncwarp();
+                const int rest = q_count - 32;
+                Entry tmp;
+                if ((int)lane < rest) tmp = q[32 + lane];
+                __syncwarp();
+                if ((int)lane < rest) q[lane] = tmp;
+                __syncwarp();
+                q_count = rest;
+                // unpark
+                phi = unpark_r<Real>(v, 0 * stride);
+                unpark_w<PREC>(v, 2 * stride, W);
+                m = (int)unpark(v, 4 * stride);
+                rec = (unsigned long long)unpark(v, 5 * stride) |
+                      ((unsigned long long)unpark(v, 6 * stride) << 32);
+                const unsigned sf = unpark(v, 7 * stride);
+                set = (int)(sf & 0x3fffffffu);
+                live = (sf & 0x40000000u) != 0u;
+                exhausted = (sf & 0x80000000u) != 0u;
+                pl.r1_x0 = unpark(v, 8 * stride);
+                pl.r1_x1 = unpark(v, 9 * stride);
+                pl.r1_set = unpark(v, 10 * stride);
+                const SetConst& S = s_sets[set];
+                model.load(S);
+                phi_end = set_phi_end<Real>(S);
+                twouv = set_twouv<Real>(S);
+                m_max = S.m_max;
             }
         }
         if (live) W.add(sblk);
     }
+    if (q_count > 0) {
+        __syncwarp();
+        replay_batch<Real, PREC, MODEL, WALL, KS>(q, q_count, P, s_sets, lane, my_steps);
+    }
 
     // ---- total steps: warp reduce, one atomic per warp ----
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_xor_sync(FULL, my_steps, o);
     if (lane == 0) {
-        atomicAdd(&scratch->steps, my_steps);
-        if (steps_out) atomicAdd(steps_out, my_steps);
+        atomicAdd(&P.scratch->steps, my_steps);
+        if (P.steps_out) atomicAdd(P.steps_out, my_steps);
     }
 }
 

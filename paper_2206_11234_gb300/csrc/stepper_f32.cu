@@ -6,16 +6,16 @@ namespace fpt {
 namespace {
 
 template <int PREC, int MODEL, bool WALL, int KS>
-cudaError_t launch(const StepperArgs& a, int grid, int block, cudaStream_t stream) {
-    stepper_kernel<float, PREC, MODEL, WALL, KS><<<grid, block, 0, stream>>>(
-        a.sets, a.n_sets, a.n_total, a.key0, a.key1, a.out_N, a.out_logw, a.scratch, a.steps_out);
+cudaError_t launch(const StepperParams& a, int grid, int block, cudaStream_t stream) {
+    const size_t smem = stepper_table_bytes(a.n_sets) + (size_t)(block / 32) * warp_smem_bytes<float, PREC>();
+    stepper_kernel<float, PREC, MODEL, WALL, KS><<<grid, block, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int PREC, int MODEL, bool WALL, int KS>
 StepperKernel make() {
     return StepperKernel{(const void*)stepper_kernel<float, PREC, MODEL, WALL, KS>,
-                         &launch<PREC, MODEL, WALL, KS>};
+                         warp_smem_bytes<float, PREC>(), &launch<PREC, MODEL, WALL, KS>};
 }
 
 template <int PREC, int MODEL, bool WALL>
@@ -24,7 +24,7 @@ StepperKernel by_ks(int ks) {
         case 8: return make<PREC, MODEL, WALL, 8>();
         case 16: return make<PREC, MODEL, WALL, 16>();
         case 32: return make<PREC, MODEL, WALL, 32>();
-        default: return StepperKernel{nullptr, nullptr};
+        default: return StepperKernel{nullptr, 0, nullptr};
     }
 }
 
@@ -37,7 +37,7 @@ template <int PREC>
 StepperKernel by_model(int model, bool wall, int ks) {
     if (model == FPT_MODEL_QUADRATIC) return by_wall<PREC, FPT_MODEL_QUADRATIC>(wall, ks);
     if (model == FPT_MODEL_CONSTANT) return by_wall<PREC, FPT_MODEL_CONSTANT>(wall, ks);
-    return StepperKernel{nullptr, nullptr};
+    return StepperKernel{nullptr, 0, nullptr};
 }
 
 }  // namespace
@@ -45,7 +45,7 @@ StepperKernel by_model(int model, bool wall, int ks) {
 StepperKernel stepper_f32(int precision, int model, bool wall, int k_steps) {
     if (precision == FPT_PREC_F32_KAHAN) return by_model<FPT_PREC_F32_KAHAN>(model, wall, k_steps);
     if (precision == FPT_PREC_F32_F64ACC) return by_model<FPT_PREC_F32_F64ACC>(model, wall, k_steps);
-    return StepperKernel{nullptr, nullptr};
+    return StepperKernel{nullptr, 0, nullptr};
 }
 
 }  // namespace fpt

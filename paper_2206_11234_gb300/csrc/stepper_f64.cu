@@ -9,16 +9,16 @@ namespace fpt {
 namespace {
 
 template <int MODEL, bool WALL, int KS>
-cudaError_t launch(const StepperArgs& a, int grid, int block, cudaStream_t stream) {
-    stepper_kernel<double, FPT_PREC_F64, MODEL, WALL, KS><<<grid, block, 0, stream>>>(
-        a.sets, a.n_sets, a.n_total, a.key0, a.key1, a.out_N, a.out_logw, a.scratch, a.steps_out);
+cudaError_t launch(const StepperParams& a, int grid, int block, cudaStream_t stream) {
+    const size_t smem = stepper_table_bytes(a.n_sets) + (size_t)(block / 32) * warp_smem_bytes<double, FPT_PREC_F64>();
+    stepper_kernel<double, FPT_PREC_F64, MODEL, WALL, KS><<<grid, block, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int MODEL, bool WALL, int KS>
 StepperKernel make() {
     return StepperKernel{(const void*)stepper_kernel<double, FPT_PREC_F64, MODEL, WALL, KS>,
-                         &launch<MODEL, WALL, KS>};
+                         warp_smem_bytes<double, FPT_PREC_F64>(), &launch<MODEL, WALL, KS>};
 }
 
 template <int MODEL, bool WALL>
@@ -26,7 +26,7 @@ StepperKernel by_ks(int ks) {
     switch (ks) {
         case 4: return make<MODEL, WALL, 4>();
         case 8: return make<MODEL, WALL, 8>();
-        default: return StepperKernel{nullptr, nullptr};
+        default: return StepperKernel{nullptr, 0, nullptr};
     }
 }
 
@@ -40,7 +40,7 @@ StepperKernel by_wall(bool wall, int ks) {
 StepperKernel stepper_f64(int model, bool wall, int k_steps) {
     if (model == FPT_MODEL_QUADRATIC) return by_wall<FPT_MODEL_QUADRATIC>(wall, k_steps);
     if (model == FPT_MODEL_CONSTANT) return by_wall<FPT_MODEL_CONSTANT>(wall, k_steps);
-    return StepperKernel{nullptr, nullptr};
+    return StepperKernel{nullptr, 0, nullptr};
 }
 
 }  // namespace fpt

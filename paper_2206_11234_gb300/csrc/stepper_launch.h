@@ -7,21 +7,15 @@
 
 namespace fpt {
 
-struct StepperArgs {
-    const SetConst* sets;
-    int n_sets;
-    unsigned long long n_total;
-    uint32_t key0, key1;
-    double* out_N;
-    double* out_logw;
-    StepperScratch* scratch;
-    unsigned long long* steps_out;
+struct StepperKernel {
+    const void* func;     // for occupancy queries; nullptr = no such instantiation
+    int warp_smem_bytes;  // dynamic shared memory per warp (replay queue + parking)
+    cudaError_t (*launch)(const StepperParams&, int grid, int block, cudaStream_t stream);
 };
 
-struct StepperKernel {
-    const void* func;  // for occupancy queries; nullptr = no such instantiation
-    cudaError_t (*launch)(const StepperArgs&, int grid, int block, cudaStream_t stream);
-};
+inline size_t stepper_smem(const StepperKernel& k, int block, int n_sets) {
+    return stepper_table_bytes(n_sets) + (size_t)(block / 32) * (size_t)k.warp_smem_bytes;
+}
 
 // Block lengths with an instantiation: binary32 8/16/32, binary64 4/8.
 StepperKernel stepper_f32(int precision, int model, bool wall, int k_steps);

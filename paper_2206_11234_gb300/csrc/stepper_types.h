@@ -3,6 +3,7 @@
 #include <cstdint>
 
 #include "fpt.h"
+#include "rng.cuh"
 
 namespace fpt {
 
@@ -25,12 +26,31 @@ struct SetConst {
     float pad_[2];
 };
 
+// Bytes of the per-set table at the start of the stepper's dynamic shared
+// memory: n_sets SetConst plus n_sets + 1 set starts, rounded to 16.
+inline __host__ __device__ size_t stepper_table_bytes(int n_sets) {
+    const size_t b = (size_t)n_sets * sizeof(SetConst) + (size_t)(n_sets + 1) * sizeof(long long);
+    return (b + 15) / 16 * 16;
+}
+
 // Device scratch of one stepper launch (zeroed before the launch).
 struct StepperScratch {
     unsigned long long ticket;  // next record index to hand out
     unsigned long long steps;   // total Euler–Maruyama steps taken
     unsigned int status;        // error flags (0 = ok)
     unsigned int pad_;
+};
+
+// Kernel parameters of one stepper launch (passed by value: constant bank).
+struct StepperParams {
+    PhiloxKeys keys;                 // round keys of the seed
+    const SetConst* sets;            // n_sets entries (device)
+    int n_sets;
+    unsigned long long n_total;      // records over all sets
+    double* out_N;
+    double* out_logw;
+    StepperScratch* scratch;         // zeroed before the launch
+    unsigned long long* steps_out;   // optional
 };
 
 }  // namespace fpt

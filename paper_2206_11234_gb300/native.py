@@ -110,12 +110,15 @@ def _load():
     L.fpt_simulate_batch_host.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
     L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
+    L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
+    L.fpt_autotune_reset.argtypes = []
+    L.fpt_autotune_reset.restype = None
     L.fpt_strerror.restype = ctypes.c_char_p
     L.fpt_strerror.argtypes = [ctypes.c_int]
     L.fpt_last_error.restype = ctypes.c_char_p
     L.fpt_abi_version.restype = ctypes.c_int
     for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
-                 "fpt_normals"):
+                 "fpt_normals", "fpt_autotune"):
         getattr(L, name).restype = ctypes.c_int
     if L.fpt_abi_version() != FPT_ABI_VERSION:
         raise ImportError("libfpt_gb300.so ABI version mismatch")
@@ -219,6 +222,20 @@ def fpt_normals(seed: int, traj: int, set_id: int, k0: int, n_blocks: int, preci
                 stream=None):
     prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
     _check(lib.fpt_normals(seed, traj, set_id, k0, n_blocks, prec, _dptr(out), _stream(stream)))
+
+
+def fpt_autotune(params: FptParams, sets: ctypes.Array, seed: int = 0, fraction: float = 0.01):
+    """Returns (block_dim, k_steps, pilot steps/s) and caches the shape in the library."""
+    b = ctypes.c_int32()
+    k = ctypes.c_int32()
+    r = ctypes.c_double()
+    _check(lib.fpt_autotune(ctypes.byref(params), sets, len(sets), seed, fraction, ctypes.byref(b),
+                            ctypes.byref(k), ctypes.byref(r)))
+    return b.value, k.value, r.value
+
+
+def fpt_autotune_reset():
+    lib.fpt_autotune_reset()
 
 
 # ---- conveniences (allocation + unpacking; no arithmetic of the method) ----
