@@ -96,6 +96,23 @@ typedef struct fpt_params {
     uint64_t* steps_out; /* optional device counter: the number of Euler–Maruyama steps taken is ADDED to it */
 } fpt_params;
 
+/* Learned bias (FPT_BIAS_MLP): b(phi, N) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3,
+ * x = ((phi - norm[0]) norm[1], (N_elapsed - norm[2]) norm[3]), 64 hidden units
+ * per layer.  The bias of the EM step is B = b(phi, N) S(phi) (§2.3 Eq. (18)
+ * with a state-dependent amplitude); b is evaluated at the start of every
+ * k_eval-step block of a run and held for the block, so the importance weight
+ * of §2.2 Eqs. (12)-(14) stays exact.  Parameters are BF16 (the bit pattern of
+ * the upper half of an IEEE float) in the order W1[64][2] (row-major), b1[64],
+ * W2[64][64] (row-major, out x in), b2[64], w3[64], b3; the vector is padded to
+ * FPT_MLP_NPARAM_PAD entries (the padding is ignored).  Device memory. */
+#define FPT_MLP_HIDDEN 64
+#define FPT_MLP_NPARAM 4417
+#define FPT_MLP_NPARAM_PAD 4424
+typedef struct fpt_mlp_params {
+    float norm[4];
+    uint16_t w[FPT_MLP_NPARAM_PAD];
+} fpt_mlp_params;
+
 /* Simulate n_traj runs of one parameter set (§2.2 Eqs. (10)-(15)).
  *   phi_in, phi_end : start and end of inflation; phi_in <= phi_end gives N = 0, ln w = 0
  *   phi_uv          : reflecting wall, >= phi_in, or +INFINITY for none
@@ -157,6 +174,19 @@ int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets,
 int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo,
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
+
+/* Batched MLP forward: out_b[i] = b(phi[i], N[i]) for i < n (device arrays,
+ * float).  The hidden 64 x 64 layer runs on the tensor cores (BF16 inputs,
+ * FP32 accumulation); the others on the CUDA cores with tanh.approx. */
+int fpt_mlp_forward(const fpt_mlp_params* w, const float* phi, const float* N, int64_t n, float* out_b,
+                    void* stream);
+
+/* Batched MLP backward: grad[j] += sum_i g[i] * d b(phi[i], N[i]) / d param_j for
+ * the FPT_MLP_NPARAM parameters in the packed order (device float array,
+ * accumulated, not cleared).  The products delta2 W2 and delta2^T h1 run on the
+ * tensor cores; the sums of the vector gradients on the CUDA cores. */
+int fpt_mlp_backward(const fpt_mlp_params* w, const float* phi, const float* N, const float* g, int64_t n,
+                     float* grad, void* stream);
 
 /* Autotuner of the stepper's launch shape (threads per block in {128, 256, 512}
  * and steps per scheduling block k_steps in {8, 16, 32}, binary64: {4, 8}).

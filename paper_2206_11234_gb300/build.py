@@ -28,6 +28,7 @@ UNITS = {
     "rng_probe.cu": ["-fmad=false"],
     "noalloc.cu": [],
     "autotune.cu": [],
+    "mlp.cu": [],
 }
 
 

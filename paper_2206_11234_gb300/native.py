@@ -111,6 +111,8 @@ def _load():
     L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
+    L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.fpt_autotune_reset.argtypes = []
     L.fpt_autotune_reset.restype = None
     L.fpt_strerror.restype = ctypes.c_char_p
@@ -118,7 +120,7 @@ def _load():
     L.fpt_last_error.restype = ctypes.c_char_p
     L.fpt_abi_version.restype = ctypes.c_int
     for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
-                 "fpt_normals", "fpt_autotune"):
+                 "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward"):
         getattr(L, name).restype = ctypes.c_int
     if L.fpt_abi_version() != FPT_ABI_VERSION:
         raise ImportError("libfpt_gb300.so ABI version mismatch")
@@ -222,6 +224,44 @@ def fpt_normals(seed: int, traj: int, set_id: int, k0: int, n_blocks: int, preci
                 stream=None):
     prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
     _check(lib.fpt_normals(seed, traj, set_id, k0, n_blocks, prec, _dptr(out), _stream(stream)))
+
+
+MLP_HIDDEN = 64
+MLP_NPARAM = 4417
+MLP_NPARAM_PAD = 4424
+MLP_BYTES = 16 + 2 * MLP_NPARAM_PAD  # sizeof(fpt_mlp_params)
+
+
+def mlp_pack(params, norm, device="cuda") -> torch.Tensor:
+    """fpt_mlp_params as a uint8 device tensor from float parameters (rounded to
+    BF16 by round-to-nearest-even) and the 4 input-normalisation constants."""
+    p = torch.as_tensor(params, dtype=torch.float32).flatten()
+    if p.numel() != MLP_NPARAM:
+        raise ValueError(f"expected {MLP_NPARAM} parameters")
+    bf = torch.zeros(MLP_NPARAM_PAD, dtype=torch.bfloat16)
+    bf[:MLP_NPARAM] = p.to(torch.bfloat16)
+    head = torch.as_tensor(norm, dtype=torch.float32).flatten()
+    buf = torch.cat([head.view(torch.uint8), bf.view(torch.uint8)])
+    assert buf.numel() == MLP_BYTES
+    return buf.to(device)
+
+
+def mlp_unpack_bf16(params) -> torch.Tensor:
+    """The float64 values the BF16-rounded parameters represent (what the GPU uses)."""
+    p = torch.as_tensor(params, dtype=torch.float32).flatten()
+    return p.to(torch.bfloat16).to(torch.float64)
+
+
+def fpt_mlp_forward(w: torch.Tensor, phi: torch.Tensor, N: torch.Tensor, out_b: torch.Tensor, stream=None):
+    _check(lib.fpt_mlp_forward(_dptr(w), _dptr(phi, torch.float32), _dptr(N, torch.float32), phi.numel(),
+                               _dptr(out_b, torch.float32), _stream(stream)))
+
+
+def fpt_mlp_backward(w: torch.Tensor, phi: torch.Tensor, N: torch.Tensor, g: torch.Tensor, grad: torch.Tensor,
+                     stream=None):
+    _check(lib.fpt_mlp_backward(_dptr(w), _dptr(phi, torch.float32), _dptr(N, torch.float32),
+                                _dptr(g, torch.float32), phi.numel(), _dptr(grad, torch.float32),
+                                _stream(stream)))
 
 
 def fpt_autotune(params: FptParams, sets: ctypes.Array, seed: int = 0, fraction: float = 0.01):
