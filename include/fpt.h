@@ -175,6 +175,29 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
 
+/* One training record of the learned-bias stepper: the MLP inputs at the start
+ * of a k_eval-step block of run `run` (its record index in the call's outputs)
+ * and the sum of the normals drawn in that block (up to the run's last step).
+ * d ln w / d b of the block is -sqrt(dN) * xi_sum. */
+typedef struct fpt_mlp_record {
+    float phi, N, xi_sum;
+    uint32_t run;
+} fpt_mlp_record;
+
+/* Simulate with the learned bias (p->bias_kind = FPT_BIAS_MLP, p->mlp = device
+ * fpt_mlp_params, p->precision = FPT_PREC_F32_F64ACC, quadratic model): as
+ * fpt_simulate_batch (no histograms; fpt_set.b is ignored) with b(phi, N)
+ * evaluated on the tensor cores for 128 runs at a time at the start of every
+ * k_eval-step block (p->k_eval in {16, 32, 64}, 0 = 32; runs start on a block
+ * boundary, so a run's evaluations are at steps 0, k_eval, 2 k_eval, ...).
+ * If records is non-NULL, one fpt_mlp_record per simulated block is appended
+ * (in no particular order) up to record_capacity; *n_records_out (host, may be
+ * NULL) receives the number of blocks simulated, and the call fails with
+ * FPT_ENOMEM if that exceeds the capacity.  Total runs must be < 2^32. */
+int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
+                     double* out_N, double* out_logw, fpt_mlp_record* records, int64_t record_capacity,
+                     int64_t* n_records_out);
+
 /* Batched MLP forward: out_b[i] = b(phi[i], N[i]) for i < n (device arrays,
  * float).  The hidden 64 x 64 layer runs on the tensor cores (BF16 inputs,
  * FP32 accumulation); the others on the CUDA cores with tanh.approx. */

@@ -29,6 +29,7 @@ UNITS = {
     "noalloc.cu": [],
     "autotune.cu": [],
     "mlp.cu": [],
+    "stepper_mlp.cu": [],
 }
 
 

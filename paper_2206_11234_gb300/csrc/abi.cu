@@ -108,6 +108,9 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
     c.traj_offset = s.traj_offset;
     c.m_max = (int)steps;
     c.set_id = s.set_id;
+    c.f_cmdN = (float)(c.cm * s.dN);
+    c.f_dN = (float)s.dN;
+    c.f_sq = (float)c.sq;
     c.f_phi_in = (float)s.phi_in;
     c.f_phi_end = (float)s.phi_end;
     c.f_twouv = (float)c.twouv;

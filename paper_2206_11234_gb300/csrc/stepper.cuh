@@ -190,36 +190,37 @@ constexpr int kParkWords = 12;  // per thread: a run's live state during a batch
 
 // Park / unpark 32-bit words through volatile shared memory, so the values are
 // really dead in registers while the replay runs (no store-to-load forwarding).
+// The slots are interleaved by thread: word j of a thread is at v[j * stride]
+// (stride = threads per block), so a 64-bit value takes words i and i + stride.
 __device__ __forceinline__ void park(volatile unsigned* v, int i, unsigned x) { v[i] = x; }
 __device__ __forceinline__ unsigned unpark(volatile unsigned* v, int i) { return v[i]; }
 __device__ __forceinline__ void park_f(volatile unsigned* v, int i, float x) { v[i] = __float_as_uint(x); }
 __device__ __forceinline__ float unpark_f(volatile unsigned* v, int i) { return __uint_as_float(v[i]); }
-__device__ __forceinline__ void park_d(volatile unsigned* v, int i, double x) {
+__device__ __forceinline__ void park_d(volatile unsigned* v, int i, int stride, double x) {
     v[i] = (unsigned)__double2loint(x);
-    v[i + 1] = (unsigned)__double2hiint(x);
+    v[i + stride] = (unsigned)__double2hiint(x);
 }
-__device__ __forceinline__ double unpark_d(volatile unsigned* v, int i) {
-    return __hiloint2double((int)v[i + 1], (int)v[i]);
-}
-template <typename Real>
-__device__ __forceinline__ void park_r(volatile unsigned* v, int i, Real x) {
-    if constexpr (sizeof(Real) == 4) park_f(v, i, (float)x); else park_d(v, i, (double)x);
+__device__ __forceinline__ double unpark_d(volatile unsigned* v, int i, int stride) {
+    return __hiloint2double((int)v[i + stride], (int)v[i]);
 }
 template <typename Real>
-__device__ __forceinline__ Real unpark_r(volatile unsigned* v, int i) {
-    if constexpr (sizeof(Real) == 4) return (Real)unpark_f(v, i); else return (Real)unpark_d(v, i);
+__device__ __forceinline__ void park_r(volatile unsigned* v, int i, int stride, Real x) {
+    if constexpr (sizeof(Real) == 4) park_f(v, i, (float)x); else park_d(v, i, stride, (double)x);
+}
+template <typename Real>
+__device__ __forceinline__ Real unpark_r(volatile unsigned* v, int i, int stride) {
+    if constexpr (sizeof(Real) == 4) return (Real)unpark_f(v, i); else return (Real)unpark_d(v, i, stride);
 }
 template <int PREC>
-__device__ __forceinline__ void park_w(volatile unsigned* v, int i, const WSum<PREC>& W) {
-    if constexpr (PREC == FPT_PREC_F32_KAHAN) { park_f(v, i, W.s); park_f(v, i + 1, W.c); }
-    else park_d(v, i, W.s);
+__device__ __forceinline__ void park_w(volatile unsigned* v, int i, int stride, const WSum<PREC>& W) {
+    if constexpr (PREC == FPT_PREC_F32_KAHAN) { park_f(v, i, W.s); park_f(v, i + stride, W.c); }
+    else park_d(v, i, stride, W.s);
 }
 template <int PREC>
-__device__ __forceinline__ void unpark_w(volatile unsigned* v, int i, WSum<PREC>& W) {
-    if constexpr (PREC == FPT_PREC_F32_KAHAN) { W.s = unpark_f(v, i); W.c = unpark_f(v, i + 1); }
-    else W.s = unpark_d(v, i);
+__device__ __forceinline__ void unpark_w(volatile unsigned* v, int i, int stride, WSum<PREC>& W) {
+    if constexpr (PREC == FPT_PREC_F32_KAHAN) { W.s = unpark_f(v, i); W.c = unpark_f(v, i + stride); }
+    else W.s = unpark_d(v, i, stride);
 }
-
 // dynamic shared memory per warp: the replay queue plus the parking slots
 template <typename Real, int PREC>
 constexpr int warp_smem_bytes() { return kQueueCap * (int)sizeof(Pending<Real, PREC>) + 32 * kParkWords * 4; }
@@ -408,10 +409,10 @@ stepper_kernel(const StepperParams P) {
             q_count += __popc(ev);
             if (q_count >= 32) {
                 // park this lane's run (the stride keeps one thread's words in one bank)
-                const unsigned stride = blockDim.x;
+                const int stride = (int)blockDim.x;
                 volatile unsigned* v = park_slot;
-                park_r<Real>(v, 0 * stride, phi);
-                park_w<PREC>(v, 2 * stride, W);  // 2 words
+                park_r<Real>(v, 0 * stride, stride, phi);  // words 0, 1
+                park_w<PREC>(v, 2 * stride, stride, W);    // words 2, 3
                 park(v, 4 * stride, (unsigned)m);
                 park(v, 5 * stride, (unsigned)rec);
                 park(v, 6 * stride, (unsigned)(rec >> 32));
@@ -430,8 +431,8 @@ stepper_kernel(const StepperParams P) {
                 __syncwarp();
                 q_count = rest;
                 // unpark
-                phi = unpark_r<Real>(v, 0 * stride);
-                unpark_w<PREC>(v, 2 * stride, W);
+                phi = unpark_r<Real>(v, 0 * stride, stride);
+                unpark_w<PREC>(v, 2 * stride, stride, W);
                 m = (int)unpark(v, 4 * stride);
                 rec = (unsigned long long)unpark(v, 5 * stride) |
                       ((unsigned long long)unpark(v, 6 * stride) << 32);

@@ -23,7 +23,8 @@ struct SetConst {
     uint32_t set_id;                        // Philox counter word 3
     float f_phi_in, f_phi_end, f_twouv;
     float f_c1, f_c2, f_c3;                 // binary32 step constants (see ModelStep)
-    float pad_[2];
+    float f_cmdN;                           // c0 m dN: the bias part of dphi/phi is b * f_cmdN
+    float f_dN, f_sq;                       // dN and sqrt(dN) in binary32 (learned-bias stepper)
 };
 
 // Bytes of the per-set table at the start of the stepper's dynamic shared

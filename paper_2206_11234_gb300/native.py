@@ -112,6 +112,7 @@ def _load():
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.fpt_simulate_mlp.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, i64, P(i64)]
     L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.fpt_autotune_reset.argtypes = []
     L.fpt_autotune_reset.restype = None
@@ -120,7 +121,7 @@ def _load():
     L.fpt_last_error.restype = ctypes.c_char_p
     L.fpt_abi_version.restype = ctypes.c_int
     for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
-                 "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward"):
+                 "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward", "fpt_simulate_mlp"):
         getattr(L, name).restype = ctypes.c_int
     if L.fpt_abi_version() != FPT_ABI_VERSION:
         raise ImportError("libfpt_gb300.so ABI version mismatch")
@@ -153,15 +154,16 @@ def _stream(stream) -> Optional[int]:
 
 def make_params(*, model=MODEL_QUADRATIC, precision=PREC_F64, m=1.0, a0=0.0, s0=0.0, n_max,
                 block_dim=0, k_steps=0, set_id=0, traj_offset=0, stream=None,
-                steps_out: Optional[torch.Tensor] = None) -> FptParams:
+                steps_out: Optional[torch.Tensor] = None, mlp: Optional[torch.Tensor] = None,
+                k_eval: int = 0) -> FptParams:
     p = FptParams()
     p.abi_version = FPT_ABI_VERSION
     p.model = model
     p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
-    p.bias_kind = BIAS_CONST
+    p.bias_kind = BIAS_CONST if mlp is None else BIAS_MLP
     p.m, p.a0, p.s0, p.n_max = m, a0, s0, n_max
-    p.mlp = None
-    p.k_eval = 0
+    p.mlp = None if mlp is None else mlp.data_ptr()
+    p.k_eval = k_eval
     p.block_dim, p.k_steps = block_dim, k_steps
     p.set_id, p.traj_offset = set_id, traj_offset
     p.stream = _stream(stream)
@@ -250,6 +252,20 @@ def mlp_unpack_bf16(params) -> torch.Tensor:
     """The float64 values the BF16-rounded parameters represent (what the GPU uses)."""
     p = torch.as_tensor(params, dtype=torch.float32).flatten()
     return p.to(torch.bfloat16).to(torch.float64)
+
+
+RECORD_FIELDS = 4  # fpt_mlp_record: phi, N, xi_sum (float32), run (uint32)
+
+
+def fpt_simulate_mlp(params: FptParams, sets: ctypes.Array, seed: int, out_N: torch.Tensor,
+                     out_logw: torch.Tensor, records: Optional[torch.Tensor] = None) -> int:
+    """Learned-bias simulation; records: float32 device tensor [capacity, 4]
+    (column 3 holds the uint32 run index bits).  Returns the number of blocks."""
+    n = ctypes.c_int64()
+    cap = 0 if records is None else records.shape[0]
+    _check(lib.fpt_simulate_mlp(ctypes.byref(params), sets, len(sets), seed, _dptr(out_N, torch.float64),
+                                _dptr(out_logw, torch.float64), _dptr(records), cap, ctypes.byref(n)))
+    return n.value
 
 
 def fpt_mlp_forward(w: torch.Tensor, phi: torch.Tensor, N: torch.Tensor, out_b: torch.Tensor, stream=None):
