@@ -198,6 +198,41 @@ int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_t n_sets, u
                      double* out_N, double* out_logw, fpt_mlp_record* records, int64_t record_capacity,
                      int64_t* n_records_out);
 
+/* Device buffers of the learned-bias training loop (owned by the caller). */
+typedef struct fpt_mlp_train_state {
+    float* master;            /* FPT_MLP_NPARAM FP32 parameters, updated in place */
+    float* adam_m;            /* FPT_MLP_NPARAM first moments (start at 0) */
+    float* adam_v;            /* FPT_MLP_NPARAM second moments (start at 0) */
+    float* grad;              /* FPT_MLP_NPARAM scratch */
+    fpt_mlp_params* w;        /* BF16 parameters the simulation uses; rewritten from master */
+    fpt_mlp_record* records;  /* record_capacity records of the step's simulation */
+    int64_t record_capacity;
+    double* out_N;            /* n_traj first-passage times of the step's runs */
+    double* out_logw;         /* n_traj log-weights */
+    double* coef;             /* n_traj scratch */
+    float* rows;              /* 3 * record_capacity scratch */
+    int32_t step;             /* Adam step counter (host; incremented by each call) */
+} fpt_mlp_train_state;
+
+typedef struct fpt_mlp_train_stats {
+    double log_second_moment; /* log of the estimate of E_S[w^2 1{N > tail_N}] before the update */
+    double p_hat;             /* estimate of P(N > tail_N) from the step's runs (§2.2 Eq. (16)) */
+    double n_eff;             /* p_hat^2 / its variance estimate */
+    double frac_in_tail;      /* fraction of sample runs with N > tail_N */
+    int64_t n_records;        /* blocks simulated */
+} fpt_mlp_train_stats;
+
+/* One Adam step on log E_S[w^2 1{N > tail_N}], the second moment of the
+ * weighted tail estimator (minimising it minimises the estimator's variance):
+ * simulate set->n_traj runs with the current BF16 parameters (p as for
+ * fpt_simulate_mlp, p->mlp == state->w) recording every block, weight run i by
+ * w_i^2 1{N_i > tail_N} / sum_j w_j^2 1{N_j > tail_N} (max-shifted), back-propagate
+ * -sqrt(dN) * xi_sum of every block through the MLP on the tensor cores and
+ * update master / w with Adam (beta 0.9, 0.999, learning rate lr).  All of it
+ * runs on the device; the call synchronises p->stream once at the end. */
+int fpt_mlp_train_step(const fpt_params* p, const fpt_set* set, uint64_t seed, double tail_N, double lr,
+                       fpt_mlp_train_state* state, fpt_mlp_train_stats* stats_out);
+
 /* Batched MLP forward: out_b[i] = b(phi[i], N[i]) for i < n (device arrays,
  * float).  The hidden 64 x 64 layer runs on the tensor cores (BF16 inputs,
  * FP32 accumulation); the others on the CUDA cores with tanh.approx. */

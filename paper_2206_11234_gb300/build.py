@@ -30,6 +30,7 @@ UNITS = {
     "autotune.cu": [],
     "mlp.cu": [],
     "stepper_mlp.cu": [],
+    "train.cu": [],
 }
 
 

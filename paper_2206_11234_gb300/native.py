@@ -85,6 +85,18 @@ class FptHistCounts(ctypes.Structure):
                 ("total", ctypes.c_int64)]
 
 
+class FptMlpTrainState(ctypes.Structure):
+    _fields_ = [("master", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("w", ctypes.c_void_p), ("records", ctypes.c_void_p),
+                ("record_capacity", ctypes.c_int64), ("out_N", ctypes.c_void_p), ("out_logw", ctypes.c_void_p),
+                ("coef", ctypes.c_void_p), ("rows", ctypes.c_void_p), ("step", ctypes.c_int32)]
+
+
+class FptMlpTrainStats(ctypes.Structure):
+    _fields_ = [("log_second_moment", ctypes.c_double), ("p_hat", ctypes.c_double), ("n_eff", ctypes.c_double),
+                ("frac_in_tail", ctypes.c_double), ("n_records", ctypes.c_int64)]
+
+
 BIN_FIELDS = 6  # an fpt_bin is 6 x 8 bytes: view bins as float64[n, 6] (count as int64 bits)
 
 
@@ -113,6 +125,8 @@ def _load():
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
     L.fpt_simulate_mlp.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, i64, P(i64)]
+    L.fpt_mlp_train_step.argtypes = [P(FptParams), P(FptSet), u64, d, d, P(FptMlpTrainState),
+                                     P(FptMlpTrainStats)]
     L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.fpt_autotune_reset.argtypes = []
     L.fpt_autotune_reset.restype = None
@@ -121,7 +135,8 @@ def _load():
     L.fpt_last_error.restype = ctypes.c_char_p
     L.fpt_abi_version.restype = ctypes.c_int
     for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
-                 "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward", "fpt_simulate_mlp"):
+                 "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward", "fpt_simulate_mlp",
+                 "fpt_mlp_train_step"):
         getattr(L, name).restype = ctypes.c_int
     if L.fpt_abi_version() != FPT_ABI_VERSION:
         raise ImportError("libfpt_gb300.so ABI version mismatch")
@@ -266,6 +281,46 @@ def fpt_simulate_mlp(params: FptParams, sets: ctypes.Array, seed: int, out_N: to
     _check(lib.fpt_simulate_mlp(ctypes.byref(params), sets, len(sets), seed, _dptr(out_N, torch.float64),
                                 _dptr(out_logw, torch.float64), _dptr(records), cap, ctypes.byref(n)))
     return n.value
+
+
+class MlpTrainer:
+    """Device buffers of fpt_mlp_train_step for one parameter set (allocation
+    and the call only; every step runs in the library's kernels)."""
+
+    def __init__(self, spec, params, norm, *, k_eval=32, device="cuda", stream=None):
+        self.spec = spec
+        self.k_eval = k_eval
+        self.norm = tuple(norm)
+        n = spec.n_traj
+        cap = int(n * (spec.n_max / spec.dN / k_eval + 2))
+        f32 = dict(dtype=torch.float32, device=device)
+        self.master = torch.as_tensor(params, dtype=torch.float32).to(device).contiguous()
+        self.adam_m = torch.zeros(MLP_NPARAM, **f32)
+        self.adam_v = torch.zeros(MLP_NPARAM, **f32)
+        self.grad = torch.zeros(MLP_NPARAM, **f32)
+        self.w = mlp_pack(self.master.cpu(), norm, device)
+        self.records = torch.empty((cap, RECORD_FIELDS), **f32)
+        self.out_N = torch.empty(n, dtype=torch.float64, device=device)
+        self.out_logw = torch.empty(n, dtype=torch.float64, device=device)
+        self.coef = torch.empty(n, dtype=torch.float64, device=device)
+        self.rows = torch.empty(3 * cap, **f32)
+        st = FptMlpTrainState()
+        st.master, st.adam_m, st.adam_v = self.master.data_ptr(), self.adam_m.data_ptr(), self.adam_v.data_ptr()
+        st.grad, st.w, st.records = self.grad.data_ptr(), self.w.data_ptr(), self.records.data_ptr()
+        st.record_capacity = cap
+        st.out_N, st.out_logw = self.out_N.data_ptr(), self.out_logw.data_ptr()
+        st.coef, st.rows, st.step = self.coef.data_ptr(), self.rows.data_ptr(), 0
+        self.state = st
+        self.sets = make_sets([spec])
+        self.params = make_params(precision=PREC_F32_F64ACC, m=spec.m, n_max=spec.n_max, mlp=self.w,
+                                  k_eval=k_eval, stream=stream)
+
+    def step(self, seed: int, tail_N: float, lr: float):
+        stats = FptMlpTrainStats()
+        _check(lib.fpt_mlp_train_step(ctypes.byref(self.params), self.sets, seed, tail_N, lr,
+                                      ctypes.byref(self.state), ctypes.byref(stats)))
+        return {"log_second_moment": stats.log_second_moment, "p_hat": stats.p_hat, "n_eff": stats.n_eff,
+                "frac_in_tail": stats.frac_in_tail, "n_records": stats.n_records}
 
 
 def fpt_mlp_forward(w: torch.Tensor, phi: torch.Tensor, N: torch.Tensor, out_b: torch.Tensor, stream=None):

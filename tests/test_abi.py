@@ -37,12 +37,15 @@ def test_struct_layouts_match_header(native, tmp_path):
     """The ctypes mirrors have the sizes and field offsets the C compiler gives
     the header's structs."""
     structs = {"fpt_params": native.FptParams, "fpt_set": native.FptSet, "fpt_bin": native.FptBin,
-               "fpt_hist_counts": native.FptHistCounts}
+               "fpt_hist_counts": native.FptHistCounts, "fpt_mlp_train_state": native.FptMlpTrainState,
+               "fpt_mlp_train_stats": native.FptMlpTrainStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fpt.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for fname, _ in cls._fields_:
             lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('printf("fpt_mlp_params %zu\\n", sizeof(fpt_mlp_params));')
+    lines.append('printf("fpt_mlp_record %zu\\n", sizeof(fpt_mlp_record));')
     lines.append("return 0; }")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -50,6 +53,8 @@ def test_struct_layouts_match_header(native, tmp_path):
     import subprocess
     subprocess.check_call(["cc", "-std=c11", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(out["fpt_mlp_params"]) == native.MLP_BYTES
+    assert int(out["fpt_mlp_record"]) == 4 * native.RECORD_FIELDS
     for cname, cls in structs.items():
         assert int(out[cname]) == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
