@@ -20,6 +20,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,7 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="drift_ladder",
-                    choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall"])
+                    choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall",
+                             "learned_bias"])
+    ap.add_argument("--train-steps", type=int, default=256, help="learned_bias: Adam steps")
+    ap.add_argument("--lr", type=float, default=2e-3, help="learned_bias: Adam learning rate")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
@@ -171,6 +176,114 @@ def cpu_oracle_rate(workload, seconds, threads=None):
     return tally["steps"] / dt, threads, sample
 
 
+def run_learned_bias(args):
+    """Learned bias vs the best constant bias on far-tail effective samples per
+    second: m = 1, phi_in = 8, reflecting wall phi_uv = 9, dN = 5e-4, tail event
+    N > 40, censored at N = 60.  A ladder of constant b (2^20 runs each) picks
+    the best b by effective samples per EM step; that b is rerun on as many
+    runs as the learned inference (2^26) for a like-for-like n_eff/s.  Training:
+    2^16 runs per Adam step, --train-steps steps (2^24 runs at the default).
+    Everything is scaled by --scale.  The FP64 oracle runs the trained network
+    on a bounded sample as a cross-check of the estimate."""
+    import torch
+    from paper_2206_11234_gb300 import native as nat
+    from paper_2206_11234_gb300 import workloads as W
+    import oracle
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    base = dict(phi_in=8.0, m=1.0, dN=5e-4, n_max=60.0, phi_uv=9.0)
+    tail = 40.0
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b) / 1e3
+
+    steps = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def constant(b, n, seed):
+        spec = W.SetSpec(n_traj=n, b=b, hist_lo=0.0, hist_hi=60.0, n_bins=512, **base)
+        wl = W.Workload(f"const b={b}", [spec], "f32_f64acc", seed=seed)
+        steps.zero_()
+        (N, lw, _, _), t = timed(lambda: nat.simulate_workload(wl, with_hist=False, steps_out=steps))
+        ne = tail_neff(N, lw, [spec], tail)[0]
+        st = int(steps.item())
+        return {"b": b, "runs": n, "P": ne["P"], "n_eff": ne["n_eff"], "seconds": t, "steps": st,
+                "steps_per_s": st / t, "n_eff_per_s": ne["n_eff"] / t, "n_eff_per_Msteps": 1e6 * ne["n_eff"] / st}
+
+    n_c = max(4096, int((1 << 20) * args.scale))
+    ladder = [constant(b, n_c, 11) for b in (0.0, 0.2, 0.4, 0.6, 0.8, 1.0, 2.0, 4.0, 6.0)]
+    best_b = max(ladder, key=lambda r: r["n_eff_per_Msteps"])["b"]
+    n_i = max(4096, int((1 << 26) * args.scale))
+    best = constant(best_b, n_i, 13)
+    # training, starting from the best constant amplitude
+    n_t = max(1024, int((1 << 16) * args.scale))
+    init = W.mlp_params(seed=5, gain=1.0, out_scale=0.05)
+    init[-1] = best_b
+    norm = (5.2, 0.5, 30.0, 1.0 / 15.0)
+    tr = nat.MlpTrainer(W.SetSpec(n_traj=n_t, b=0.0, **base), init, norm, k_eval=32, stream=stream)
+    hist = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(args.train_steps):
+        hist.append(tr.step(seed=100000 + it, tail_N=tail, lr=args.lr))
+    train_s = time.perf_counter() - t0
+    # inference with the trained network
+    spec = W.SetSpec(n_traj=n_i, b=0.0, **base)
+    sets = nat.make_sets([spec])
+    N = torch.empty(n_i, dtype=torch.float64, device=dev)
+    lw = torch.empty(n_i, dtype=torch.float64, device=dev)
+    p = nat.make_params(precision="f32_f64acc", m=1.0, n_max=60.0, mlp=tr.w, k_eval=32, stream=stream,
+                        steps_out=steps)
+    nat.fpt_simulate_mlp(p, sets, 77, N[:4096], lw[:4096])  # warm-up
+    steps.zero_()
+    _, t_inf = timed(lambda: nat.fpt_simulate_mlp(p, sets, 12345, N, lw))
+    ne = tail_neff(N, lw, [spec], tail)[0]
+    st = int(steps.item())
+    learned = {"runs": n_i, "P": ne["P"], "n_eff": ne["n_eff"], "seconds": t_inf, "steps": st,
+               "steps_per_s": st / t_inf, "n_eff_per_s": ne["n_eff"] / t_inf,
+               "n_eff_per_Msteps": 1e6 * ne["n_eff"] / st,
+               "train_seconds": train_s, "train_runs": n_t * args.train_steps,
+               "rel_second_moment_log_first": hist[0]["log_second_moment"] - 2 * math.log(max(hist[0]["p_hat"], 1e-300)),
+               "rel_second_moment_log_last": hist[-1]["log_second_moment"] - 2 * math.log(max(hist[-1]["p_hat"], 1e-300))}
+    # FP64 oracle with the same (BF16) network on a bounded sample, all host cores
+    p64 = nat.mlp_unpack_bf16(tr.master.cpu()).numpy()
+    n_o = 1024
+    res = [None] * 16
+
+    def work(t):
+        r = oracle.make_run(m=1.0, phi_in=8.0, phi_uv=9.0, dN=5e-4, n_max=60.0, seed=999, traj_offset=t * (n_o // 16),
+                            mlp=p64, mlp_norm=norm, k_eval=32)
+        res[t] = oracle.simulate(r, n_o // 16)
+    ths = [threading.Thread(target=work, args=(t,)) for t in range(16)]
+    t0 = time.perf_counter()
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    No = np.concatenate([r[0] for r in res])
+    lo = np.concatenate([r[1] for r in res])
+    xo = np.where(No > tail, np.exp(lo), 0.0)
+    orc = {"runs": n_o, "P": float(xo.mean()), "se": float(xo.std() / math.sqrt(n_o)),
+           "seconds": time.perf_counter() - t0}
+    se_gpu = math.sqrt(max(ne["P"] ** 2 / max(ne["n_eff"], 1e-300), 0.0))
+    line = {"metric": METRIC, "value": learned["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * t_inf, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "learned bias vs constant: m=1 phi_in=8 phi_uv=9 dN=5e-4, tail N > 40",
+                       "scale": args.scale, "train_steps": args.train_steps, "lr": args.lr},
+            "tail": {"event": f"N > {tail}", "reference_P_survival_pde": 1.0986e-3,
+                     "best_constant": best, "learned": learned, "learned_se": se_gpu, "oracle_learned": orc,
+                     "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None},
+            "ladder": ladder}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -203,6 +316,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "learned_bias":
+        return run_learned_bias(args)
 
     import torch
     import torch.distributed as dist
@@ -244,9 +359,12 @@ def main():
         tb, tk, trate = nat.fpt_autotune(params(wl.precision), sets, seed=99, fraction=0.02)
         tuned = {"block_dim": tb, "k_steps": tk, "pilot_steps_per_s": trate}
     p = params(wl.precision, steps_ctr)
+    # one graph-captured launch per step: stepper over all sets + histograms
+    plan = nat.Plan(p, sets, N, lw, bins, counts)
+    plan_stepper = nat.Plan(p, sets, N, lw)
 
     def one_step(seed):
-        nat.fpt_simulate_batch(p, sets, seed, N, lw, bins, counts)
+        plan.launch(seed, stream)
 
     for i in range(args.warmup):
         one_step(1000 + i)
@@ -287,7 +405,7 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         for i in range(args.steps):
-            nat.fpt_simulate_batch(p, sets, i, N, lw, None, None)
+            plan_stepper.launch(i, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_stepper = e0.elapsed_time(e1) / args.steps
@@ -296,7 +414,7 @@ def main():
     extra = {}
     if rank == 0:
         # far-tail effective samples (E = {N > tail_N}) of the last timed step's runs
-        nat.fpt_simulate_batch(p, sets, args.steps - 1, N, lw, bins, counts)
+        plan.launch(args.steps - 1, stream)
         if wl.tail_N is not None:
             ne = tail_neff(N, lw, specs, wl.tail_N)
             best = max(ne, key=lambda r: r["n_eff"])
@@ -390,6 +508,7 @@ def main():
                    "parallelism": f"dp{world} (disjoint run ids per GPU)",
                    "launch_shape": tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}},
         "gpu_launches": 5 * args.steps,
+        "launch": "one CUDA graph per step (fpt_plan: scratch reset, stepper, 4 histogram kernels)",
         "clocks": clk.summary(),
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -165,6 +165,23 @@ int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets,
                        double* out_N, double* out_logw, fpt_bin* out_bins,
                        fpt_hist_counts* out_counts);
 
+/* Reusable, graph-captured batched launch.  fpt_plan_create validates the
+ * sets once, uploads their constants to a plan-owned device workspace and
+ * captures [scratch reset, persistent stepper, histogram kernels (if out_bins),
+ * status copy] into one CUDA graph writing to the given device outputs (laid
+ * out as in fpt_simulate_batch); the stepper's launch shape is fixed at
+ * creation (p->block_dim / k_steps, or the autotuned shape).
+ * fpt_plan_launch(plan, seed, stream) sets the seed and replays the graph on
+ * `stream` (the device current at creation), then synchronises it and checks
+ * the device status; results equal fpt_simulate_batch's with the same seed.
+ * fpt_plan_destroy frees the plan.  A plan is not safe for concurrent launches. */
+typedef struct fpt_plan fpt_plan;
+int fpt_plan_create(const fpt_params* p, const fpt_set* sets, int32_t n_sets, double* out_N,
+                    double* out_logw, fpt_bin* out_bins, fpt_hist_counts* out_counts,
+                    fpt_plan** plan_out);
+int fpt_plan_launch(fpt_plan* plan, uint64_t seed, void* stream);
+int fpt_plan_destroy(fpt_plan* plan);
+
 /* Weighted histogram of n records.  Bins (lo + j d, lo + (j+1) d],
  * d = (hi - lo)/n_bins, j = ceil((N - lo)/d) - 1 clamped to [0, n_bins).
  * Record i (global id id_offset + i) goes to subset (id_offset + i) mod n_sub

@@ -31,6 +31,7 @@ UNITS = {
     "mlp.cu": [],
     "stepper_mlp.cu": [],
     "train.cu": [],
+    "plan.cu": [],
 }
 
 

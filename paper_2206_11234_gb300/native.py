@@ -125,6 +125,9 @@ def _load():
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
     L.fpt_simulate_mlp.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, i64, P(i64)]
+    L.fpt_plan_create.argtypes = [P(FptParams), P(FptSet), i32, vp, vp, vp, vp, P(vp)]
+    L.fpt_plan_launch.argtypes = [vp, u64, vp]
+    L.fpt_plan_destroy.argtypes = [vp]
     L.fpt_mlp_train_step.argtypes = [P(FptParams), P(FptSet), u64, d, d, P(FptMlpTrainState),
                                      P(FptMlpTrainStats)]
     L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
@@ -136,7 +139,7 @@ def _load():
     L.fpt_abi_version.restype = ctypes.c_int
     for name in ("fpt_simulate", "fpt_simulate_batch", "fpt_simulate_batch_host", "fpt_histogram",
                  "fpt_normals", "fpt_autotune", "fpt_mlp_forward", "fpt_mlp_backward", "fpt_simulate_mlp",
-                 "fpt_mlp_train_step"):
+                 "fpt_mlp_train_step", "fpt_plan_create", "fpt_plan_launch", "fpt_plan_destroy"):
         getattr(L, name).restype = ctypes.c_int
     if L.fpt_abi_version() != FPT_ABI_VERSION:
         raise ImportError("libfpt_gb300.so ABI version mismatch")
@@ -215,6 +218,33 @@ def fpt_simulate_batch(params: FptParams, sets: ctypes.Array, seed: int, out_N: 
     _check(lib.fpt_simulate_batch(ctypes.byref(params), sets, len(sets), seed,
                                   _dptr(out_N, torch.float64), _dptr(out_logw, torch.float64),
                                   _dptr(out_bins), _dptr(out_counts)))
+
+
+class Plan:
+    """A graph-captured batched launch (fpt_plan_*) writing into fixed device tensors."""
+
+    def __init__(self, params: FptParams, sets: ctypes.Array, out_N: torch.Tensor, out_logw: torch.Tensor,
+                 out_bins: Optional[torch.Tensor] = None, out_counts: Optional[torch.Tensor] = None):
+        self._keep = (sets, out_N, out_logw, out_bins, out_counts)
+        h = ctypes.c_void_p()
+        _check(lib.fpt_plan_create(ctypes.byref(params), sets, len(sets), _dptr(out_N, torch.float64),
+                                   _dptr(out_logw, torch.float64), _dptr(out_bins), _dptr(out_counts),
+                                   ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, seed: int, stream=None):
+        _check(lib.fpt_plan_launch(self.handle, seed, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib.fpt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fpt_simulate_batch_host(params: FptParams, sets: ctypes.Array, seed: int, host_N, host_logw,

@@ -150,3 +150,37 @@ def test_invalid_arguments_are_rejected_before_launch(nat):
     p = nat.make_params(precision="f32_kahan", m=1.0, n_max=6.0, k_steps=12)
     with pytest.raises(nat.FptError):
         nat.fpt_simulate(p, 8, 3.0, math.sqrt(2), math.inf, 1e-3, 1.0, 0, x, x)
+
+
+def test_graph_plan_reproduces_batched_call(nat):
+    """The graph-captured plan equals fpt_simulate_batch for two seeds in a row."""
+    import torch
+    wl = W.batched_uneven(scale=1 / 1024)
+    specs = wl.sets[::4]
+    sets = nat.make_sets(specs)
+    n = sum(s.n_traj for s in specs)
+    nb = sum(s.n_bins for s in specs)
+    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    lw = torch.empty(n, dtype=torch.float64, device="cuda")
+    bins = nat.empty_bins(nb)
+    counts = nat.empty_counts(len(specs))
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+    p = nat.make_params(precision="f32_kahan", m=1.0, n_max=10.0, k_steps=32, steps_out=steps)
+    plan = nat.Plan(p, sets, N, lw, bins, counts)
+    for seed in (5, 6):
+        steps.zero_()
+        plan.launch(seed)
+        got = (N.clone(), lw.clone(), counts.clone(), int(steps.item()))
+        f_plan, c_plan = nat.bins_to_numpy(bins)
+        steps.zero_()
+        q = nat.make_params(precision="f32_kahan", m=1.0, n_max=10.0, k_steps=32, steps_out=steps)
+        N2 = torch.empty_like(N)
+        l2 = torch.empty_like(lw)
+        b2 = nat.empty_bins(nb)
+        c2 = nat.empty_counts(len(specs))
+        nat.fpt_simulate_batch(q, sets, seed, N2, l2, b2, c2)
+        assert torch.equal(got[0], N2) and torch.equal(got[1], l2) and torch.equal(got[2], c2)
+        assert got[3] == int(steps.item())
+        f2, cc2 = nat.bins_to_numpy(b2)
+        assert np.array_equal(c_plan, cc2) and np.array_equal(f_plan[:, 0], f2[:, 0])
+    plan.close()
