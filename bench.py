@@ -240,7 +240,8 @@ def run_learned_bias(args):
     lw = torch.empty(n_i, dtype=torch.float64, device=dev)
     p = nat.make_params(precision="f32_f64acc", m=1.0, n_max=60.0, mlp=tr.w, k_eval=32, stream=stream,
                         steps_out=steps)
-    nat.fpt_simulate_mlp(p, sets, 77, N[:4096], lw[:4096])  # warm-up
+    warm = nat.make_sets([W.SetSpec(n_traj=min(n_i, 65536), b=0.0, **base)])
+    nat.fpt_simulate_mlp(p, warm, 77, N, lw)  # warm-up
     steps.zero_()
     _, t_inf = timed(lambda: nat.fpt_simulate_mlp(p, sets, 12345, N, lw))
     ne = tail_neff(N, lw, [spec], tail)[0]

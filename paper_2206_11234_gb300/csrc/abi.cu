@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -211,6 +212,29 @@ int stepper_grid(const StepperKernel& k, int block, int n_sets, unsigned long lo
     const unsigned long long full = (unsigned long long)per_sm * n_sm;
     const unsigned long long need = (n_total + block - 1) / block;
     *grid = (int)(need < full ? (need < 1 ? 1 : need) : full);
+    return FPT_OK;
+}
+
+int resident_ctas(const void* func, int threads, size_t dyn_smem, int tmem_cols, int* per_sm) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    int dev = 0, smem_sm = 0, reserved = 0, max_blocks = 0, regs_sm = 0, max_threads = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&max_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const size_t smem_block = dyn_smem + fa.sharedSizeBytes + (size_t)reserved;
+    const int warps = (threads + 31) / 32;
+    const int regs_block = ((fa.numRegs * 32 + 255) / 256) * 256 * warps;  // 256-register warp granules
+    int n = max_blocks;
+    n = std::min(n, (int)((size_t)smem_sm / smem_block));
+    n = std::min(n, regs_block > 0 ? regs_sm / regs_block : n);
+    n = std::min(n, max_threads / threads);
+    if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
+    *per_sm = n;
     return FPT_OK;
 }
 

@@ -15,6 +15,10 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int device_sm_count(int* n_sm);
 int check_params(const fpt_params* p);
+// CTAs of `func` that fit on one SM by registers, shared memory, threads and
+// (tmem_cols > 0) the 512 TMEM columns; computed from the kernel's attributes,
+// since the occupancy API is conservative for kernels that allocate TMEM.
+int resident_ctas(const void* func, int threads, size_t dyn_smem, int tmem_cols, int* per_sm);
 
 // Host-side image of one batched call.
 struct Prepared {

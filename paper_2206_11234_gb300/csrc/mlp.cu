@@ -238,10 +238,9 @@ int mlp_grid(const void* func, size_t smem, int tmem_cols, long long tiles, int*
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "MLP kernel shared memory");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, 128, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "MLP occupancy");
+    rc = resident_ctas(func, 128, smem, tmem_cols, &per_sm);
+    if (rc) return rc;
     if (per_sm < 1) return fail(FPT_EUNSUPPORTED, "MLP kernel does not fit on an SM");
-    if (per_sm * tmem_cols > 512) return fail(FPT_EUNSUPPORTED, "MLP kernel: %d CTAs x %d TMEM columns", per_sm, tmem_cols);
     const long long full = (long long)per_sm * n_sm;
     *grid = (int)(tiles < full ? (tiles < 1 ? 1 : tiles) : full);
     return FPT_OK;

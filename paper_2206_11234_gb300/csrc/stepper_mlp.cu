@@ -317,15 +317,11 @@ int launch_mlp(const StepperParams& a, const fpt_mlp_params* W, const RecordSink
     if (rc) return rc;
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "learned-bias stepper shared memory");
+    // every resident CTA holds kMlpTmemCols TMEM columns until it exits
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, 128, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "learned-bias stepper occupancy");
+    rc = resident_ctas(func, 128, smem, kMlpTmemCols, &per_sm);
+    if (rc) return rc;
     if (per_sm < 1) return fail(FPT_EUNSUPPORTED, "learned-bias stepper does not fit on an SM");
-    // every resident CTA holds kMlpTmemCols TMEM columns until it exits: the
-    // shared memory per CTA must keep the resident CTAs within the 512 columns
-    if (per_sm * kMlpTmemCols > 512)
-        return fail(FPT_EUNSUPPORTED, "learned-bias stepper: %d resident CTAs x %d TMEM columns", per_sm,
-                    kMlpTmemCols);
     const unsigned long long full = (unsigned long long)per_sm * n_sm;
     const unsigned long long need = (a.n_total + 127) / 128;
     const int grid = (int)(need < full ? (need < 1 ? 1 : need) : full);
