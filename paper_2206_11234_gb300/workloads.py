@@ -35,6 +35,7 @@ class SetSpec:
     model: int = 0  # 0 quadratic, 1 constant drift/noise test model
     a0: float = 0.0
     s0: float = 0.0
+    traj_offset: int = 0  # id of the set's first run (sharding across ranks)
 
 
 @dataclasses.dataclass

@@ -1,0 +1,87 @@
+"""Multi-rank path on the CPU: two gloo ranks each simulate their shard of the
+run ids (with the FP64 oracle standing in for a GPU) and merge histograms;
+the result equals the one-process run exactly (records, counts, maxima) and
+to 1e-12 (sums)."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11234_gb300 import shard
+from paper_2206_11234_gb300 import workloads as W
+
+SPEC = dict(phi_in=3.0, m=1.0, b=0.8, dN=2e-3, n_max=6.0, n_traj=3001, phi_uv=3.6, hist_lo=0.0, hist_hi=6.0,
+            n_bins=60)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _run(spec):
+    r = oracle.make_run(m=spec.m, phi_in=spec.phi_in, phi_uv=spec.phi_uv, dN=spec.dN, b=spec.b, n_max=spec.n_max,
+                        traj_offset=spec.traj_offset)
+    N, lw, _ = oracle.simulate(r, spec.n_traj)
+    bins, counts = oracle.histogram(N, lw, spec.n_bins, spec.hist_lo, spec.hist_hi, id_offset=spec.traj_offset)
+    return N, lw, bins[0], counts
+
+
+def _worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    spec = W.SetSpec(**SPEC)
+    mine = shard.shard_sets([spec], rank, world)[0]
+    N, lw, bins, counts = _run(mine)
+    f, c = shard.allgather_merge(bins[:, :5], bins[:, 5].astype(np.int64))
+    np.savez(os.path.join(out_dir, f"r{rank}.npz"), N=N, lw=lw, off=mine.traj_offset, f=f, c=c,
+             cnt=counts)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_match_one_process(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    full = W.SetSpec(**SPEC)
+    N, lw, bins, counts = _run(full)
+    parts = [np.load(os.path.join(tmp_path, f"r{r}.npz")) for r in range(world)]
+    # records: the shards are the one-process records, bit for bit
+    cat_N = np.concatenate([p["N"] for p in parts])
+    cat_lw = np.concatenate([p["lw"] for p in parts])
+    assert np.array_equal(cat_N, N) and np.array_equal(cat_lw, lw)
+    for p in parts:
+        f, c = p["f"], p["c"]
+        assert np.array_equal(c, bins[:, 5].astype(np.int64))
+        assert np.array_equal(f[:, 0], bins[:, 0])
+        np.testing.assert_allclose(f[:, 1:3], bins[:, 1:3], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(f[:, 3:5], bins[:, 3:5], rtol=1e-12, atol=1e-12 * np.abs(bins[:, 3:5]).max())
+    assert sum(int(p["cnt"][3]) for p in parts) == counts[3]
+
+
+def test_shard_ranges_partition_the_ids():
+    spec = W.SetSpec(**SPEC)
+    for world in (1, 2, 3, 8):
+        shards = [shard.shard_sets([spec], r, world)[0] for r in range(world)]
+        assert sum(s.n_traj for s in shards) == spec.n_traj
+        starts = [s.traj_offset for s in shards]
+        assert starts == sorted(starts) and starts[0] == 0
+        for a, b in zip(shards, shards[1:]):
+            assert a.traj_offset + a.n_traj == b.traj_offset
+    with pytest.raises(ValueError):
+        shard.shard_sets([spec], 2, 2)
+
+
+def test_merge_handles_empty_bins():
+    f1 = np.array([[-np.inf, 0, 0, 0, 0], [1.0, 2.0, 3.0, 4.0, 5.0]])
+    f2 = np.array([[0.5, 1.0, 1.0, 0.5, 0.25], [-np.inf, 0, 0, 0, 0]])
+    f, c = shard.merge_bins([f1, f2], [np.array([0, 2]), np.array([1, 0])])
+    assert np.array_equal(c, [1, 2])
+    assert f[0, 0] == 0.5 and f[0, 1] == 1.0 and f[1, 1] == 2.0
