@@ -115,13 +115,16 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
     c.f_phi_in = (float)s.phi_in;
     c.f_phi_end = (float)s.phi_end;
     c.f_twouv = (float)c.twouv;
+    // binary32 step constants; the noise coefficient carries -sqrt(2 ln 2), the
+    // factor between the stepper's Box–Muller radius rho and the normal (rng.cuh)
+    const double neg_sqrt2ln2 = -1.1774100225154747;
     if (p->model == FPT_MODEL_QUADRATIC) {
-        c.f_c1 = (float)(s.b * c.cm * s.dN);  // bias part of dphi/phi
-        c.f_c2 = (float)(c.cm * c.sq);        // noise part of dphi/phi per unit xi
-        c.f_c3 = (float)(-2.0 * s.dN);        // drift part of dphi, times phi
+        c.f_c1 = (float)(s.b * c.cm * s.dN);                 // bias part of dphi/phi
+        c.f_c2 = (float)(neg_sqrt2ln2 * c.cm * c.sq);        // noise part of dphi/phi per unit rho cos
+        c.f_c3 = (float)(-2.0 * s.dN);                       // drift part of dphi, times phi
     } else {
         c.f_c1 = (float)((p->a0 + s.b * p->s0) * s.dN);
-        c.f_c2 = (float)(p->s0 * c.sq);
+        c.f_c2 = (float)(neg_sqrt2ln2 * p->s0 * c.sq);
         c.f_c3 = 0.0f;
     }
     *out = c;

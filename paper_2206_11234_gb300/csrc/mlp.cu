@@ -137,10 +137,12 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
                 float d[2];
+                const int n0 = 16 * c + e;
+                const uint32_t hh = tc::tanh_bf16x2(tc::pack_bf16(z[e] + S.b2[n0], z[e + 1] + S.b2[n0 + 1]));
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int nn = 16 * c + e + u;
-                    const float h2 = tc::tanh_approx(z[e + u] + S.b2[nn]);
+                    const int nn = n0 + u;
+                    const float h2 = u == 0 ? tc::bf16_lo(hh) : tc::bf16_hi(hh);
                     d[u] = gi * S.w3[nn] * (1.f - h2 * h2);
                     store_bf16(B.D2T, tc::kmajor_offset(nn, tid, 128), d[u]);
                     const float sw3 = warp_sum(gi * h2);

@@ -71,7 +71,8 @@ __device__ __forceinline__ void mlp_fwd_load(MlpFwdSmem& S, const fpt_mlp_params
     __syncthreads();
 }
 
-// First layer of row `row` (this thread) into the A tile: h1 = tanh(W1 x + b1).
+// First layer of row `row` (this thread) into the A tile: h1 = tanh(W1 x + b1),
+// two units per MUFU operation (bf16x2 tanh; the tile holds bf16 anyway).
 __device__ __forceinline__ void mlp_layer1_to_tile(const MlpFwdSmem& S, unsigned char* A, int row, float x0,
                                                    float x1) {
 #pragma unroll
@@ -80,9 +81,9 @@ __device__ __forceinline__ void mlp_layer1_to_tile(const MlpFwdSmem& S, unsigned
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int j = 8 * c + 2 * p;
-            const float h0 = tc::tanh_approx(fmaf(S.w1[j][0], x0, fmaf(S.w1[j][1], x1, S.b1[j])));
-            const float h1 = tc::tanh_approx(fmaf(S.w1[j + 1][0], x0, fmaf(S.w1[j + 1][1], x1, S.b1[j + 1])));
-            q[p] = tc::pack_bf16(h0, h1);
+            const float a0 = fmaf(S.w1[j][0], x0, fmaf(S.w1[j][1], x1, S.b1[j]));
+            const float a1 = fmaf(S.w1[j + 1][0], x0, fmaf(S.w1[j + 1][1], x1, S.b1[j + 1]));
+            q[p] = tc::tanh_bf16x2(tc::pack_bf16(a0, a1));
         }
         *reinterpret_cast<uint4*>(A + tc::kmajor_offset(row, 8 * c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
     }
@@ -121,7 +122,12 @@ __device__ __forceinline__ float mlp_forward_tile(MlpFwdSmem& S, float phi, floa
         tc::tmem_ld16(taddr + 16 * c, z);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) b = fmaf(S.w3[16 * c + i], tc::tanh_approx(z[i] + S.b2[16 * c + i]), b);
+        for (int i = 0; i < 16; i += 2) {  // h2 = tanh(z + b2), two units per MUFU operation
+            const int n = 16 * c + i;
+            const uint32_t h = tc::tanh_bf16x2(tc::pack_bf16(z[i] + S.b2[n], z[i + 1] + S.b2[n + 1]));
+            b = fmaf(S.w3[n], tc::bf16_lo(h), b);
+            b = fmaf(S.w3[n + 1], tc::bf16_hi(h), b);
+        }
     }
     tc::fence_before_sync();
     return b;

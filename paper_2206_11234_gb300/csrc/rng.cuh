@@ -118,10 +118,16 @@ __device__ __forceinline__ void normals4_f64(const PhiloxLane& l, uint32_t k, co
 // ---- Box–Muller, binary32 (hardware approximations) ----
 // u = ((w >> 9) + 1/2) 2^-23 is exact in binary32: put the top 23 bits into
 // the mantissa of 1.0 (a shift-add, the bits do not overlap) and subtract
-// 1 - 2^-24 (exact by Sterbenz).  The angle is
-// taken as 2 pi u - pi in [-pi, pi), where the fast sine/cosine are accurate;
-// sin(2 pi u - pi) = -sin(2 pi u) and likewise for cos, so the sign is folded
-// into r.  The result tracks the binary64 normals to ~1e-6.
+// 1 - 2^-24 (exact by Sterbenz).  The radius is r = sqrt(-2 ln u0) =
+// sqrt(2 ln 2) * rho with rho = sqrt(-log2 u0); the angle is taken as
+// 2 pi u1 - pi in [-pi, pi), where the fast sine/cosine are accurate, and
+// sin(2 pi u1 - pi) = -sin(2 pi u1), likewise for cos.  A pair of normals is
+// therefore  xi0 = -sqrt(2 ln 2) rho c,  xi1 = -sqrt(2 ln 2) rho s  with
+// (c, s) = (cos, sin)(2 pi u1 - pi).  The stepper works with (rho, c, s) and
+// folds the constant -sqrt(2 ln 2) into its own per-run constants, so it never
+// forms xi; the values track the binary64 normals to ~1e-6.
+constexpr float kSqrt2Ln2 = 1.1774100225154747f;
+
 __device__ __forceinline__ float uniform_f32(uint32_t w) {
     return __int_as_float((w >> 9) + 0x3f800000u) - (1.0f - 0x1p-24f);
 }
@@ -132,24 +138,34 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1) {
-    const float u0 = uniform_f32(w0);
-    const float u1 = uniform_f32(w1);
-    // -2 ln u0 = (-2 ln 2) log2 u0
-    const float neg_r = -sqrt_approx(-1.3862943611198906f * __log2f(u0));
-    const float angle = __fmaf_rn(6.283185307179586f, u1, -3.14159265358979f);
-    float s, c;
-    __sincosf(angle, &s, &c);
-    z0 = neg_r * c;
-    z1 = neg_r * s;
+struct NormalPair {
+    float rho;  // sqrt(-log2 u0)
+    float c;    // cos(2 pi u1 - pi)
+    float s;    // sin(2 pi u1 - pi)
+};
+
+__device__ __forceinline__ NormalPair normal_pair_f32(uint32_t w0, uint32_t w1) {
+    NormalPair p;
+    p.rho = sqrt_approx(-__log2f(uniform_f32(w0)));
+    // 2 pi u1 - pi = 2 pi f - (pi + 2 pi (1 - 2^-24)) with f = 1 + (w1 >> 9) 2^-23: one rounding
+    const float f = __int_as_float((w1 >> 9) + 0x3f800000u);
+    const float angle = __fmaf_rn(6.283185307179586f, f, -9.424777586f);
+    __sincosf(angle, &p.s, &p.c);
+    return p;
 }
 
+// The four normals of one Philox block as values (probe / tests only).
 __device__ __forceinline__ void normals4_f32(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
                                              float xi[4]) {
     uint32_t w[4];
     philox_block(l, k, K, w);
-    box_muller_f32(w[0], w[1], xi[0], xi[1]);
-    box_muller_f32(w[2], w[3], xi[2], xi[3]);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const NormalPair q = normal_pair_f32(w[2 * p], w[2 * p + 1]);
+        const float r = -kSqrt2Ln2 * q.rho;
+        xi[2 * p] = r * q.c;
+        xi[2 * p + 1] = r * q.s;
+    }
 }
 
 }  // namespace fpt

@@ -42,39 +42,64 @@ template <typename Real, int MODEL>
 struct ModelStep;
 
 // Quadratic potential, binary32.  The increment is formed on its own and then
-// added: dphi = phi (b c m dN + c m sqrt(dN) xi) - 2 dN / phi.  (Folding the
-// bias into a factor 1 + b c m dN would round b c m dN ~ 1e-6 on the 2^-23
-// grid of numbers near 1, i.e. change b by ~1%, which the weights would not
-// know about.)  Explicit intrinsics fix the rounding so the replay of a block
+// added: dphi = phi t - 2 dN / phi with t = b c m dN + c m sqrt(dN) xi.
+// (Folding the bias into a factor 1 + b c m dN would round b c m dN ~ 1e-6 on
+// the 2^-23 grid of numbers near 1, i.e. change b by ~1%, which the weights
+// would not know about.)  t is formed from a Box–Muller pair as
+// fma(kq rho, c, tc) with kq = -sqrt(2 ln 2) c m sqrt(dN) (rng.cuh), so xi is
+// never formed.  Explicit intrinsics fix the rounding so the replay of a block
 // reproduces it bit for bit.
 template <>
 struct ModelStep<float, FPT_MODEL_QUADRATIC> {
-    float bcmdN, cmsq, m2dN;
+    float tc, kq, m2dN;  // tc = b c m dN (the bias part of t), kq, m2dN = -2 dN
     __device__ __forceinline__ void load(const SetConst& s) {
-        bcmdN = s.f_c1;
-        cmsq = s.f_c2;
+        tc = s.f_c1;
+        kq = s.f_c2;
         m2dN = s.f_c3;
     }
-    __device__ __forceinline__ float step(float phi, float xi) const {
+    __device__ __forceinline__ float step(float phi, float t) const {
         const float inv = rcp_approx(phi);
-        const float t = __fmaf_rn(cmsq, xi, bcmdN);
         const float v = __fmul_rn(m2dN, inv);
         return __fadd_rn(phi, __fmaf_rn(phi, t, v));
     }
 };
 
-// Constant drift a0 and noise s0, binary32: dphi = (a0 + b s0) dN + s0 sqrt(dN) xi.
+// Constant drift a0 and noise s0, binary32: dphi = t = (a0 + b s0) dN + s0 sqrt(dN) xi.
 template <>
 struct ModelStep<float, FPT_MODEL_CONSTANT> {
-    float c, s0sq;
+    float tc, kq;  // tc = (a0 + b s0) dN, kq = -sqrt(2 ln 2) s0 sqrt(dN)
     __device__ __forceinline__ void load(const SetConst& s) {
-        c = s.f_c1;
-        s0sq = s.f_c2;
+        tc = s.f_c1;
+        kq = s.f_c2;
     }
-    __device__ __forceinline__ float step(float phi, float xi) const {
-        return __fadd_rn(phi, __fmaf_rn(s0sq, xi, c));
-    }
+    __device__ __forceinline__ float step(float phi, float t) const { return __fadd_rn(phi, t); }
 };
+
+// Four binary32 EM steps from one Philox block (two Box–Muller pairs): the
+// state update, the wall, the block minimum and the running sum of
+// rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
+template <int MODEL, bool WALL>
+__device__ __forceinline__ void steps4_f32(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t k,
+                                           const PhiloxKeys& keys, float twouv, float& phi, float& mn,
+                                           float& srho) {
+    uint32_t w[4];
+    philox_block(pl, k, keys, w);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
+        const float q = __fmul_rn(model.kq, np.rho);
+        phi = model.step(phi, __fmaf_rn(q, np.c, model.tc));
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        mn = fminf(mn, phi);
+        phi = model.step(phi, __fmaf_rn(q, np.s, model.tc));
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        mn = fminf(mn, phi);
+        srho = __fmaf_rn(np.rho, np.c + np.s, srho);
+    }
+}
+
+// The binary32 sums are kept in units of -1/sqrt(2 ln 2) of the sum of the normals.
+constexpr double kXiPerRho = -1.1774100225154747;  // -sqrt(2 ln 2)
 
 // Binary64 (reference) steps: the update exactly as written in Eq. (11).  This
 // translation unit is compiled without FMA contraction, so each operation is
@@ -246,27 +271,55 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
     bool crossed = false;
     const uint32_t k0 = (uint32_t)e.m0 >> 2;
     for (int g = 0; g < KS / 4; ++g) {
-        Real xi[4];
-        normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
+        if constexpr (sizeof(Real) == 4) {
+            uint32_t w[4];
+            philox_block(pl, k0 + (uint32_t)g, P.keys, w);
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-            if (M == 0) {
-                prev = ph;
-                ph = model.step(ph, xi[q4]);
-                if constexpr (WALL) ph = real_min<Real>(ph, twouv - ph);
-                s2 += xi[q4];
-                const int step_index = e.m0 + 4 * g + q4;
-                if (ph <= phi_end) {
-                    crossed = true;
-                    M = step_index + 1;
-                } else if (step_index + 1 >= S.m_max) {
-                    M = step_index + 1;
+            for (int p = 0; p < 2; ++p) {
+                const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
+                const float q = __fmul_rn(model.kq, np.rho);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (M == 0) {
+                        const float trig = h == 0 ? np.c : np.s;
+                        prev = ph;
+                        ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                        if constexpr (WALL) ph = fminf(ph, twouv - ph);
+                        s2 = __fmaf_rn(np.rho, trig, s2);
+                        const int step_index = e.m0 + 4 * g + 2 * p + h;
+                        if (ph <= phi_end) {
+                            crossed = true;
+                            M = step_index + 1;
+                        } else if (step_index + 1 >= S.m_max) {
+                            M = step_index + 1;
+                        }
+                    }
+                }
+            }
+        } else {
+            Real xi[4];
+            normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                if (M == 0) {
+                    prev = ph;
+                    ph = model.step(ph, xi[q4]);
+                    if constexpr (WALL) ph = real_min<Real>(ph, twouv - ph);
+                    s2 += xi[q4];
+                    const int step_index = e.m0 + 4 * g + q4;
+                    if (ph <= phi_end) {
+                        crossed = true;
+                        M = step_index + 1;
+                    } else if (step_index + 1 >= S.m_max) {
+                        M = step_index + 1;
+                    }
                 }
             }
         }
         if (__all_sync(mask, M != 0)) break;
     }
-    const double Wtot = e.W.total(s2);
+    // sum of the normals (binary32 sums are in rho units)
+    const double Wtot = sizeof(Real) == 4 ? kXiPerRho * e.W.total(s2) : (double)e.W.total(s2);
     double N;
     if (crossed) {
         // linear interpolation of the crossing inside step M-1, in binary64
@@ -382,14 +435,18 @@ stepper_kernel(const StepperParams P) {
         const uint32_t k0 = (uint32_t)m0 >> 2;
 #pragma unroll
         for (int g = 0; g < KS / 4; ++g) {
-            Real xi[4];
-            normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
+            if constexpr (sizeof(Real) == 4) {
+                steps4_f32<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
+            } else {
+                Real xi[4];
+                normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                phi = model.step(phi, xi[q4]);
-                if constexpr (WALL) phi = real_min<Real>(phi, twouv - phi);  // mirror at phi_uv
-                mn = real_min<Real>(mn, phi);
-                sblk += xi[q4];
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    phi = model.step(phi, xi[q4]);
+                    if constexpr (WALL) phi = real_min<Real>(phi, twouv - phi);  // mirror at phi_uv
+                    mn = real_min<Real>(mn, phi);
+                    sblk += xi[q4];
+                }
             }
         }
         m = m0 + KS;

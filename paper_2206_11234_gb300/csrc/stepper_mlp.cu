@@ -69,7 +69,7 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
     const SetConst& S = s_sets[have ? e.set : 0];
     ModelStep<float, FPT_MODEL_QUADRATIC> model;
     model.load(S);
-    model.bcmdN = __fmul_rn(e.b, S.f_cmdN);
+    model.tc = __fmul_rn(e.b, S.f_cmdN);
     const float phi_end = S.f_phi_end, twouv = S.f_twouv;
     const PhiloxLane pl = philox_lane(S.traj_offset + (e.rec - (unsigned long long)S.first), S.set_id, P.keys);
     float ph = e.phi0, prev = e.phi0, s2 = 0.f;
@@ -78,21 +78,27 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
     const uint32_t k0 = (uint32_t)e.m0 >> 2;
     if (have) {
         for (int g = 0; g < KS / 4; ++g) {
-            float xi[4];
-            normals4<float>(pl, k0 + (uint32_t)g, P.keys, xi);
+            uint32_t w[4];
+            philox_block(pl, k0 + (uint32_t)g, P.keys, w);
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                if (M == 0) {
-                    prev = ph;
-                    ph = model.step(ph, xi[q4]);
-                    ph = fminf(ph, twouv - ph);
-                    s2 += xi[q4];
-                    const int step_index = e.m0 + 4 * g + q4;
-                    if (ph <= phi_end) {
-                        crossed = true;
-                        M = step_index + 1;
-                    } else if (step_index + 1 >= S.m_max) {
-                        M = step_index + 1;
+            for (int p = 0; p < 2; ++p) {
+                const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
+                const float q = __fmul_rn(model.kq, np.rho);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (M == 0) {
+                        const float trig = h == 0 ? np.c : np.s;
+                        prev = ph;
+                        ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                        ph = fminf(ph, twouv - ph);
+                        s2 = __fmaf_rn(np.rho, trig, s2);
+                        const int step_index = e.m0 + 4 * g + 2 * p + h;
+                        if (ph <= phi_end) {
+                            crossed = true;
+                            M = step_index + 1;
+                        } else if (step_index + 1 >= S.m_max) {
+                            M = step_index + 1;
+                        }
                     }
                 }
             }
@@ -100,11 +106,12 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
         }
     }
     __syncwarp();
-    emit_records(sink, have, e.phi0, __fmul_rn((float)e.m0, S.f_dN), s2, e.rec);
+    const float xisum = -kSqrt2Ln2 * s2;  // the block's sum of normals up to the last step
+    emit_records(sink, have, e.phi0, __fmul_rn((float)e.m0, S.f_dN), xisum, e.rec);
     if (!have) return;
     const float bsq = __fmul_rn(e.b, S.f_sq);
     const float hb2 = __fmul_rn(0.5f * e.b, __fmul_rn(e.b, S.f_dN));
-    const double lw = e.lw + (double)(-bsq * s2 - hb2 * (float)(M - e.m0));
+    const double lw = e.lw + (double)(-bsq * xisum - hb2 * (float)(M - e.m0));
     double N;
     if (crossed) {
         const double a = (double)prev, c = (double)ph, pe = (double)phi_end;
@@ -202,25 +209,17 @@ __global__ void __launch_bounds__(128) stepper_mlp_kernel(const StepperParams P,
         // ---- the learned bias at the block start, 128 runs per tensor-core tile ----
         const SetConst& S = s_sets[set];
         const float b = mlp_forward_tile(F, phi, __fmul_rn((float)m, S.f_dN), phase);
-        model.bcmdN = __fmul_rn(b, S.f_cmdN);
+        model.tc = __fmul_rn(b, S.f_cmdN);
 
         // ---- one block of KS steps ----
         const float phi0 = phi;
         const int m0 = m;
-        float mn = phi, sblk = 0.f;
+        float mn = phi, srho = 0.f;
         const uint32_t k0 = (uint32_t)m0 >> 2;
 #pragma unroll
-        for (int g = 0; g < KS / 4; ++g) {
-            float xi[4];
-            normals4<float>(pl, k0 + (uint32_t)g, P.keys, xi);
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                phi = model.step(phi, xi[q4]);
-                phi = fminf(phi, twouv - phi);
-                mn = fminf(mn, phi);
-                sblk += xi[q4];
-            }
-        }
+        for (int g = 0; g < KS / 4; ++g)
+            steps4_f32<FPT_MODEL_QUADRATIC, true>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
+        const float sblk = -kSqrt2Ln2 * srho;  // the block's sum of normals
         m = m0 + KS;
         const bool event = live && (mn <= phi_end || m >= m_max);
         const bool through = live && !event;
