@@ -48,6 +48,8 @@ def parse():
                              "learned_bias"])
     ap.add_argument("--train-steps", type=int, default=256, help="learned_bias: Adam steps")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned_bias: Adam learning rate")
+    ap.add_argument("--k-eval", type=int, default=64, choices=(16, 32, 64, 128),
+                    help="learned_bias: steps between two evaluations of the bias network")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
@@ -226,7 +228,7 @@ def run_learned_bias(args):
     init = W.mlp_params(seed=5, gain=1.0, out_scale=0.05)
     init[-1] = best_b
     norm = (5.2, 0.5, 30.0, 1.0 / 15.0)
-    tr = nat.MlpTrainer(W.SetSpec(n_traj=n_t, b=0.0, **base), init, norm, k_eval=32, stream=stream)
+    tr = nat.MlpTrainer(W.SetSpec(n_traj=n_t, b=0.0, **base), init, norm, k_eval=args.k_eval, stream=stream)
     hist = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -238,7 +240,7 @@ def run_learned_bias(args):
     sets = nat.make_sets([spec])
     N = torch.empty(n_i, dtype=torch.float64, device=dev)
     lw = torch.empty(n_i, dtype=torch.float64, device=dev)
-    p = nat.make_params(precision="f32_f64acc", m=1.0, n_max=60.0, mlp=tr.w, k_eval=32, stream=stream,
+    p = nat.make_params(precision="f32_f64acc", m=1.0, n_max=60.0, mlp=tr.w, k_eval=args.k_eval, stream=stream,
                         steps_out=steps)
     warm = nat.make_sets([W.SetSpec(n_traj=min(n_i, 65536), b=0.0, **base)])
     nat.fpt_simulate_mlp(p, warm, 77, N, lw)  # warm-up
@@ -259,7 +261,7 @@ def run_learned_bias(args):
 
     def work(t):
         r = oracle.make_run(m=1.0, phi_in=8.0, phi_uv=9.0, dN=5e-4, n_max=60.0, seed=999, traj_offset=t * (n_o // 16),
-                            mlp=p64, mlp_norm=norm, k_eval=32)
+                            mlp=p64, mlp_norm=norm, k_eval=args.k_eval)
         res[t] = oracle.simulate(r, n_o // 16)
     ths = [threading.Thread(target=work, args=(t,)) for t in range(16)]
     t0 = time.perf_counter()
@@ -277,7 +279,8 @@ def run_learned_bias(args):
             "warmup": 1, "ms_per_step": 1e3 * t_inf, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "learned bias vs constant: m=1 phi_in=8 phi_uv=9 dN=5e-4, tail N > 40",
-                       "scale": args.scale, "train_steps": args.train_steps, "lr": args.lr},
+                       "scale": args.scale, "train_steps": args.train_steps, "lr": args.lr,
+                       "k_eval": args.k_eval},
             "tail": {"event": f"N > {tail}", "reference_P_survival_pde": 1.0986e-3,
                      "best_constant": best, "learned": learned, "learned_se": se_gpu, "oracle_learned": orc,
                      "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None},

@@ -205,7 +205,7 @@ typedef struct fpt_mlp_record {
  * fpt_mlp_params, p->precision = FPT_PREC_F32_F64ACC, quadratic model): as
  * fpt_simulate_batch (no histograms; fpt_set.b is ignored) with b(phi, N)
  * evaluated on the tensor cores for 128 runs at a time at the start of every
- * k_eval-step block (p->k_eval in {16, 32, 64}, 0 = 32; runs start on a block
+ * k_eval-step block (p->k_eval in {16, 32, 64, 128}, 0 = 32; runs start on a block
  * boundary, so a run's evaluations are at steps 0, k_eval, 2 k_eval, ...).
  * If records is non-NULL, one fpt_mlp_record per simulated block is appended
  * (in no particular order) up to record_capacity; *n_records_out (host, may be

@@ -29,13 +29,13 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const fpt_mlp_params* 
                                                           const float* __restrict__ N, long long n,
                                                           float* __restrict__ out_b, unsigned* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char s_raw[];
-    MlpFwdSmem& S = *reinterpret_cast<MlpFwdSmem*>(s_raw);
+    MlpTile& S = *reinterpret_cast<MlpTile*>(s_raw);
     if ((threadIdx.x >> 5) == 0) {
         tc::tmem_alloc(&S.tmem, kFwdTmemCols);
         tc::tmem_relinquish();
         tc::fence_before_sync();
     }
-    mlp_fwd_load(S, P);  // ends with __syncthreads (also publishes S.tmem)
+    mlp_tile_load(S, P);  // ends with __syncthreads (also publishes S.tmem)
     tc::fence_after_sync();
     uint32_t phase = 0;
     const long long tiles = (n + 127) / 128;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const fpt_mlp_params* 
         const long long i = t * 128 + threadIdx.x;
         const float p = i < n ? phi[i] : 0.f;
         const float x = i < n ? N[i] : 0.f;
-        const float b = mlp_forward_tile(S, p, x, phase);
+        const float b = mlp_tile_forward(S, p, x, phase);
         if (i < n) out_b[i] = b;
         __syncthreads();
     }
@@ -262,7 +262,7 @@ int run_status(unsigned* d_status, cudaStream_t st) {
 }  // namespace
 
 size_t mlp_fwd_smem_bytes() {
-    return sizeof(MlpFwdSmem) > kFwdMinSmem ? sizeof(MlpFwdSmem) + 1024 : kFwdMinSmem + 1024;
+    return sizeof(MlpTile) > kFwdMinSmem ? sizeof(MlpTile) : kFwdMinSmem;
 }
 
 }  // namespace fpt

@@ -128,15 +128,19 @@ template <int KS>
 __global__ void __launch_bounds__(128) stepper_mlp_kernel(const StepperParams P, const fpt_mlp_params* __restrict__ W,
                                                           const RecordSink sink) {
     extern __shared__ __align__(1024) unsigned char s_dyn[];
-    MlpFwdSmem& F = *reinterpret_cast<MlpFwdSmem*>(s_dyn);
-    const size_t off_sets = (sizeof(MlpFwdSmem) + 15) / 16 * 16;
+    MlpTile& F = *reinterpret_cast<MlpTile*>(s_dyn);
+    const size_t off_sets = (sizeof(MlpTile) + 15) / 16 * 16;
     SetConst* s_sets = reinterpret_cast<SetConst*>(s_dyn + off_sets);
     const int n_sets = P.n_sets;
     long long* s_first = reinterpret_cast<long long*>(s_dyn + off_sets + (size_t)n_sets * sizeof(SetConst));
     unsigned char* s_queue = s_dyn + off_sets + stepper_table_bytes(n_sets);
     const unsigned tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u, lt_mask = (1u << lane) - 1u;
     PendingMlp* q = reinterpret_cast<PendingMlp*>(s_queue) + warp * kQueueCap;
-    volatile unsigned* v = reinterpret_cast<volatile unsigned*>(s_queue + 4 * kQueueCap * sizeof(PendingMlp)) + tid;
+    // lane state parked during a replay lives in the MLP's A tile, which holds
+    // nothing between two bias evaluations (mlp_tile_forward waits for the
+    // last MMA that reads it)
+    static_assert(sizeof(F.A) >= 128 * 10 * 4, "park area");
+    volatile unsigned* v = reinterpret_cast<volatile unsigned*>(F.A) + tid;
 
     if (warp == 0) {
         tc::tmem_alloc(&F.tmem, kMlpTmemCols);
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(128) stepper_mlp_kernel(const StepperParams P,
         s_first[i] = P.sets[i].first;
     }
     if (tid == 0) s_first[n_sets] = (long long)P.n_total;
-    mlp_fwd_load(F, W);  // ends with __syncthreads
+    mlp_tile_load(F, W);  // ends with __syncthreads
     tc::fence_after_sync();
 
     const unsigned FULL = 0xffffffffu;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(128) stepper_mlp_kernel(const StepperParams P,
 
         // ---- the learned bias at the block start, 128 runs per tensor-core tile ----
         const SetConst& S = s_sets[set];
-        const float b = mlp_forward_tile(F, phi, __fmul_rn((float)m, S.f_dN), phase);
+        const float b = mlp_tile_forward(F, phi, __fmul_rn((float)m, S.f_dN), phase);
         model.tc = __fmul_rn(b, S.f_cmdN);
 
         // ---- one block of KS steps ----
@@ -300,10 +304,7 @@ __global__ void __launch_bounds__(128) stepper_mlp_kernel(const StepperParams P,
 }
 
 size_t stepper_mlp_smem(int n_sets) {
-    const size_t park_bytes = (size_t)128 * 10 * 4;
-    const size_t b = (sizeof(MlpFwdSmem) + 15) / 16 * 16 + stepper_table_bytes(n_sets) +
-                     4 * kQueueCap * sizeof(PendingMlp) + park_bytes;
-    return b + 1024;
+    return (sizeof(MlpTile) + 15) / 16 * 16 + stepper_table_bytes(n_sets) + 4 * kQueueCap * sizeof(PendingMlp);
 }
 
 template <int KS>
@@ -346,7 +347,8 @@ extern "C" int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_
         return fail(FPT_EUNSUPPORTED, "the learned bias runs with FPT_PREC_F32_F64ACC");
     if (p->model != FPT_MODEL_QUADRATIC) return fail(FPT_EUNSUPPORTED, "the learned bias runs on the quadratic model");
     const int ks = p->k_eval ? p->k_eval : 32;
-    if (ks != 16 && ks != 32 && ks != 64) return fail(FPT_EINVAL, "k_eval %d not in {16, 32, 64}", ks);
+    if (ks != 16 && ks != 32 && ks != 64 && ks != 128)
+        return fail(FPT_EINVAL, "k_eval %d not in {16, 32, 64, 128}", ks);
     if (record_capacity < 0) return fail(FPT_EINVAL, "record_capacity < 0");
     fpt_params q = *p;
     q.bias_kind = FPT_BIAS_CONST;  // the generic checks below treat the set data only
@@ -389,7 +391,8 @@ extern "C" int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_
     if (!rc) {
         if (ks == 16) rc = launch_mlp<16>(a, W, sink, a.n_sets, st);
         else if (ks == 32) rc = launch_mlp<32>(a, W, sink, a.n_sets, st);
-        else rc = launch_mlp<64>(a, W, sink, a.n_sets, st);
+        else if (ks == 64) rc = launch_mlp<64>(a, W, sink, a.n_sets, st);
+        else rc = launch_mlp<128>(a, W, sink, a.n_sets, st);
     }
     StepperScratch host;
     unsigned long long count = 0;

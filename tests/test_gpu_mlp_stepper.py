@@ -49,10 +49,11 @@ def _run(nat, n, seed=0, records=True, k_eval=32, phi_in=3.0, phi_uv=4.0, dN=1e-
     return w, N, lw, (rec[:nrec] if records else None), nrec
 
 
-def test_log_weight_equals_sum_over_recorded_blocks(nat):
+@pytest.mark.parametrize("ks", [16, 32, 64, 128])
+def test_log_weight_equals_sum_over_recorded_blocks(nat, ks):
     import torch
-    n, dN, ks = 1 << 18, 1e-3, 32  # more runs than resident lanes: refills and parked replays
-    w, N, lw, rec, nrec = _run(nat, n)
+    n, dN = 1 << 18, 1e-3  # more runs than resident lanes: refills and parked replays
+    w, N, lw, rec, nrec = _run(nat, n, k_eval=ks)
     assert nrec == rec.shape[0] > n
     phi0 = rec[:, 0].contiguous()
     N0 = rec[:, 1].contiguous()
