@@ -12,7 +12,12 @@ Parity status of each function (what pins it is listed in the tests):
   simulate           pinned: inverse-Gaussian law (constant model), <N> and
                      Var N from the backward equations, E[w] = 1, log w = 0 at
                      b = 0, the brute-force path likelihood ratio
-  histogram          pinned: brute-force binning with numpy.digitize
+  histogram          pinned: brute-force binning with numpy.digitize; moments
+                     of ln w - max_lw against numpy mean / var
+  estimate (module)  pinned: scipy.stats normaltest / skewtest / kurtosistest;
+                     lognormal mean and error-bar coverage on lognormal
+                     weights; reduction to the direct estimate at w = 1 with the
+                     binomial error; hand-computed jackknife examples
   mlp_forward/back   pinned: torch.nn on CPU in float64, finite differences
   grad_pass          pinned: finite differences of the path log-likelihood
 """
@@ -151,10 +156,11 @@ def path(run, index, max_steps):
 
 
 def histogram(N, logw, n_bins, lo, hi, n_sub=1, id_offset=0):
-    """Returns (bins[n_sub, n_bins, 6], counts[4]); fields max_lw, s1, s2, l1, l2, count."""
+    """Returns (bins[n_sub, n_bins, 8], counts[4]); fields max_lw, s1, s2, l1, l2, l3, l4,
+    count, where l_k = sum (ln w - max_lw)^k."""
     N = np.ascontiguousarray(N, dtype=np.float64)
     logw = np.ascontiguousarray(logw, dtype=np.float64)
-    bins = np.zeros((n_sub, n_bins, 6))
+    bins = np.zeros((n_sub, n_bins, 8))
     counts = np.zeros(4, dtype=np.int64)
     rc = lib().oracle_histogram(_ptr(N, ctypes.c_double), _ptr(logw, ctypes.c_double), N.size,
                                 n_bins, lo, hi, n_sub, id_offset, _ptr(bins, ctypes.c_double),

@@ -298,8 +298,8 @@ int oracle_histogram(const double* N, const double* logw, int64_t n, int32_t n_b
     const double d = (hi - lo) / (double)n_bins;
     const int64_t nb = (int64_t)n_bins * n_sub;
     for (int64_t b = 0; b < nb; ++b) {
-        bins[6 * b + 0] = -INFINITY;
-        for (int f = 1; f < 6; ++f) bins[6 * b + f] = 0.0;
+        bins[8 * b + 0] = -INFINITY;
+        for (int f = 1; f < 8; ++f) bins[8 * b + f] = 0.0;
     }
     counts[0] = counts[1] = counts[2] = 0;
     counts[3] = n;
@@ -313,9 +313,9 @@ int oracle_histogram(const double* N, const double* logw, int64_t n, int32_t n_b
         if (j > n_bins - 1) j = n_bins - 1;
         int64_t s = (int64_t)((id_offset + (uint64_t)i) % (uint64_t)n_sub);
         int64_t b = s * n_bins + j;
-        if (logw[i] > bins[6 * b + 0]) bins[6 * b + 0] = logw[i];
+        if (logw[i] > bins[8 * b + 0]) bins[8 * b + 0] = logw[i];
     }
-    /* pass 2: sums */
+    /* pass 2: sums of powers of the shifted log-weight x = lw - max_lw <= 0 */
     for (int64_t i = 0; i < n; ++i) {
         if (!(N[i] < INFINITY) || N[i] <= lo || N[i] > hi) continue;
         int64_t j = (int64_t)ceil((N[i] - lo) / d) - 1;
@@ -323,12 +323,14 @@ int oracle_histogram(const double* N, const double* logw, int64_t n, int32_t n_b
         if (j > n_bins - 1) j = n_bins - 1;
         int64_t s = (int64_t)((id_offset + (uint64_t)i) % (uint64_t)n_sub);
         int64_t b = s * n_bins + j;
-        double mx = bins[6 * b + 0];
-        bins[6 * b + 1] += exp(logw[i] - mx);
-        bins[6 * b + 2] += exp(2.0 * (logw[i] - mx));
-        bins[6 * b + 3] += logw[i];
-        bins[6 * b + 4] += logw[i] * logw[i];
-        bins[6 * b + 5] += 1.0;
+        double x = logw[i] - bins[8 * b + 0];
+        bins[8 * b + 1] += exp(x);
+        bins[8 * b + 2] += exp(2.0 * x);
+        bins[8 * b + 3] += x;
+        bins[8 * b + 4] += x * x;
+        bins[8 * b + 5] += x * x * x;
+        bins[8 * b + 6] += x * x * x * x;
+        bins[8 * b + 7] += 1.0;
     }
     return 0;
 }

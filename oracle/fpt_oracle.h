@@ -75,8 +75,10 @@ int64_t oracle_path(const oracle_run* run, int64_t index, int64_t max_steps, dou
 /* Weighted histogram of first-passage times (§2.1 Eq. (9), §2.2 Eq. (16)).
  * bins: (lo + j d, lo + (j+1) d], d = (hi - lo)/n_bins.  Run i (global id
  * id_offset + i) goes to subset (id_offset + i) mod n_sub.  For each
- * (subset, bin) the output holds 6 doubles:
- *   {max_lw, s1 = sum exp(lw - max_lw), s2 = sum exp(2 (lw - max_lw)), l1 = sum lw, l2 = sum lw^2, count}
+ * (subset, bin) the output holds 8 doubles:
+ *   {max_lw, s1 = sum exp(x), s2 = sum exp(2 x), l1 = sum x, l2 = sum x^2, l3 = sum x^3,
+ *    l4 = sum x^4, count} with x = lw - max_lw (the moments feed the lognormal estimator and
+ *   the normality test of §2.3, Eqs. (27)-(29)).
  * counts[4] = {under (N <= lo), over (lo < ... N > hi, finite), censored (N not finite), total}. */
 int oracle_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo,
                      double hi, int32_t n_sub, uint64_t id_offset, double* bins, int64_t* counts);

@@ -220,7 +220,7 @@ def test_biased_and_direct_histograms_agree():
     b1, _ = oracle.histogram(N1, lw1, nb, lo, hi)
     compared = 0
     for j in range(nb):
-        c0, c1 = b0[0, j, 5], b1[0, j, 5]
+        c0, c1 = b0[0, j, 7], b1[0, j, 7]
         if c0 < 400 or c1 < 400:
             continue
         p0 = c0 / (n * width)

@@ -1,0 +1,124 @@
+"""Pins of the oracle's per-bin estimators (oracle/estimate.py): the normality
+test against scipy.stats on the same samples, the lognormal estimate and the
+coverage of its error bars on exactly lognormal weights (§2.4 Eqs. (22)-(24)),
+the reduction of the weighted estimates to the direct one when w = 1 (§2.2
+Eq. (16) -> §2.1 Eq. (9)) with the binomial standard error, and the
+jackknife of §2.1 on hand-computed examples.  CPU only."""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from oracle import estimate as E
+
+stats = pytest.importorskip("scipy.stats")
+
+
+@pytest.mark.parametrize("n", [8, 9, 20, 57, 500, 20000])
+@pytest.mark.parametrize("dist", ["normal", "lognormal", "uniform", "student3", "exponential"])
+def test_dagostino_pearson_matches_scipy(n, dist):
+    rng = np.random.default_rng(n * 7 + len(dist))
+    x = {"normal": lambda: rng.normal(-40.0, 0.7, n), "lognormal": lambda: rng.lognormal(0.0, 0.8, n),
+         "uniform": lambda: rng.uniform(-1.0, 1.0, n), "student3": lambda: rng.standard_t(3, n),
+         "exponential": lambda: rng.exponential(2.0, n)}[dist]()
+    g, b2, z1, z2, k2, p = E.dagostino_pearson(x)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        zs = stats.skewtest(x).statistic
+        zk = stats.kurtosistest(x).statistic
+        nt = stats.normaltest(x)
+    assert math.isclose(g, stats.skew(x), rel_tol=1e-9, abs_tol=1e-12)
+    assert math.isclose(b2, stats.kurtosis(x, fisher=False), rel_tol=1e-9)
+    assert math.isclose(z1, zs, rel_tol=1e-9, abs_tol=1e-10)
+    assert math.isclose(z2, zk, rel_tol=1e-9, abs_tol=1e-10)
+    assert math.isclose(k2, nt.statistic, rel_tol=1e-9, abs_tol=1e-10)
+    assert math.isclose(p, nt.pvalue, rel_tol=1e-9, abs_tol=1e-300)
+
+
+def test_lognormal_estimate_and_error_coverage():
+    """ln w ~ Normal(mu, sigma^2) in one bin: <w> = exp(mu + sigma^2/2) (Eq. (22));
+    the interval [P - eps_lo, P + eps_hi] (Eq. (24)) covers the truth about 68 %
+    of the time.  Dropping the sigma^4 term would cover ~51 %."""
+    mu, sig, n, reps = -3.0, 1.5, 60, 600
+    truth = math.exp(mu + 0.5 * sig * sig)
+    rng = np.random.default_rng(1)
+    hit, est = 0, []
+    for r in range(reps):
+        lw = rng.normal(mu, sig, n)
+        o = E.estimate(np.full(n, 0.5), lw, 1, 0.0, 1.0)
+        p, lo, hi = o["p_lognormal"][0], o["eps_lo"][0], o["eps_hi"][0]
+        hit += (p - lo <= truth <= p + hi)
+        est.append(p)
+        assert math.isclose(o["mean_lw"][0], lw.mean(), rel_tol=1e-12)
+        assert math.isclose(o["var_lw"][0], lw.var(ddof=1), rel_tol=1e-12)
+    cover = hit / reps
+    assert 0.62 <= cover <= 0.74, cover
+    assert abs(np.mean(est) / truth - 1) < 0.03
+
+
+def test_unit_weights_reduce_to_direct_estimate():
+    """w = 1 for every run (b = 0): Eq. (16) and Eq. (23) both give Eq. (9),
+    n_j / (d n_total), with the binomial standard error."""
+    rng = np.random.default_rng(2)
+    n, nb, lo, hi = 5000, 25, 0.0, 5.0
+    N = rng.gamma(3.0, 0.6, n)
+    N[rng.random(n) < 0.03] = np.inf
+    o = E.estimate(N, np.zeros(n), nb, lo, hi)
+    d = (hi - lo) / nb
+    edges = np.linspace(lo, hi, nb + 1)
+    cnt = np.histogram(N[np.isfinite(N) & (N > lo) & (N <= hi)], bins=edges)[0]
+    np.testing.assert_array_equal(o["count"], cnt)
+    q = cnt / n
+    np.testing.assert_allclose(o["p_direct"], q / d, rtol=1e-12)
+    np.testing.assert_allclose(o["se_direct"], np.sqrt(q * (1 - q) / n) / d, rtol=1e-9, atol=1e-15)
+    ok = cnt >= 2
+    np.testing.assert_allclose(o["p_lognormal"][ok], q[ok] / d, rtol=1e-12)
+    assert np.all(o["eps_lo"][ok] == 0) and np.all(o["eps_hi"][ok] == 0)
+    assert np.all(np.isnan(o["p_normal"]))  # zero variance: the test is undefined
+
+
+def test_jackknife_hand_examples():
+    """Four runs in one bin (0, 1], weights 1, 2, 1, 4 (ids 0..3), two subsets
+    by id parity: subset 0 = {1, 1} -> P0 = 2/2 = 1, subset 1 = {2, 4} -> P1 =
+    6/2 = 3; the spread (unbiased) is sqrt(2), scaled by 1/sqrt(2): 1.  The
+    full estimate is 8/4 = 2.  With ids 1..4 the subsets swap."""
+    N = np.full(4, 0.5)
+    lw = np.log([1.0, 2.0, 1.0, 4.0])
+    o = E.estimate(N, lw, 1, 0.0, 1.0, n_sub=2)
+    assert math.isclose(o["p_direct"][0], 2.0, rel_tol=1e-15)
+    assert math.isclose(o["jk_direct"][0], 1.0, rel_tol=1e-14)
+    o1 = E.estimate(N, lw, 1, 0.0, 1.0, n_sub=2, id_offset=1)
+    assert math.isclose(o1["jk_direct"][0], 1.0, rel_tol=1e-14)
+    # three subsets of 5 runs (ids 2..6 -> subsets 2, 0, 1, 2, 0): totals 2, 1, 2;
+    # weights 3, 1, 2, 5, 1 -> P0 = (1 + 1)/2 = 1, P1 = 2/1 = 2, P2 = (3 + 5)/2 = 4;
+    # mean 7/3, unbiased variance ((4/3)^2 + (1/3)^2 + (5/3)^2)/2 = 7/3, scaled by 1/sqrt(3)
+    lw3 = np.log([3.0, 1.0, 2.0, 5.0, 1.0])
+    o3 = E.estimate(np.full(5, 0.5), lw3, 1, 0.0, 1.0, n_sub=3, id_offset=2)
+    assert math.isclose(o3["jk_direct"][0], math.sqrt(7.0 / 3.0) / math.sqrt(3.0), rel_tol=1e-14)
+    np.testing.assert_array_equal(E.subset_totals(5, 3, 2), [2, 1, 2])
+
+
+def test_jackknife_agrees_with_standard_error_statistically():
+    """Direct sampling: the jackknife over 20 subsets and the analytic standard
+    error estimate the same binomial spread (bins with >= 400 runs, §2.1)."""
+    rng = np.random.default_rng(3)
+    n = 200000
+    N = rng.gamma(4.0, 0.5, n)
+    o = E.estimate(N, np.zeros(n), 20, 0.0, 6.0, n_sub=20)
+    ok = o["count"] >= 400
+    r = o["jk_direct"][ok] / o["se_direct"][ok]
+    assert ok.sum() >= 10
+    assert 0.85 < np.median(r) < 1.15 and np.all((r > 0.4) & (r < 1.8))
+
+
+def test_edge_cases():
+    N = np.array([0.5, 1.5, 1.6, np.inf, -1.0])
+    lw = np.array([-2.0, -1.0, -3.0, 0.0, 0.0])
+    o = E.estimate(N, lw, 3, 0.0, 3.0, n_sub=2)
+    assert o["count"].tolist() == [1, 2, 0]
+    assert math.isnan(o["p_lognormal"][0])          # one run: no variance
+    assert math.isclose(o["p_direct"][0], math.exp(-2.0) / 5.0)
+    assert o["p_direct"][2] == 0 and o["p_lognormal"][2] == 0 and o["eps_hi"][2] == 0
+    assert np.all(np.isnan(o["k2"]))                # fewer than 8 runs
+    assert math.isnan(o["jk_lognormal"][1])         # subset 1 holds one run of bin 1

@@ -18,7 +18,7 @@ def _brute_histogram(N, lw, n_bins, lo, hi, n_sub=1, id_offset=0):
     inside = fin & (N > lo) & (N <= hi)
     j = np.digitize(N, edges, right=True) - 1  # right-closed bins (t_j, t_{j+1}]
     sub = (id_offset + np.arange(N.size)) % n_sub
-    out = np.zeros((n_sub, n_bins, 6))
+    out = np.zeros((n_sub, n_bins, 8))
     out[:, :, 0] = -np.inf
     for s in range(n_sub):
         for b in range(n_bins):
@@ -27,8 +27,9 @@ def _brute_histogram(N, lw, n_bins, lo, hi, n_sub=1, id_offset=0):
                 continue
             x = lw[sel]
             mx = x.max()
-            out[s, b] = [mx, np.exp(x - mx).sum(), np.exp(2 * (x - mx)).sum(), x.sum(),
-                         (x * x).sum(), sel.sum()]
+            y = x - mx
+            out[s, b] = [mx, np.exp(y).sum(), np.exp(2 * y).sum(), y.sum(), (y ** 2).sum(),
+                         (y ** 3).sum(), (y ** 4).sum(), sel.sum()]
     counts = [int((fin & (N <= lo)).sum()), int((fin & (N > hi)).sum()), int((~fin).sum()), N.size]
     return out, np.array(counts)
 
@@ -39,26 +40,35 @@ def test_histogram_matches_brute_force(n_sub, id_offset):
     got, counts = oracle.histogram(N, lw, 40, 1.0, 4.0, n_sub=n_sub, id_offset=id_offset)
     ref, rc = _brute_histogram(N, lw, 40, 1.0, 4.0, n_sub=n_sub, id_offset=id_offset)
     assert np.array_equal(counts, rc)
-    assert np.array_equal(got[..., 5], ref[..., 5])
+    assert np.array_equal(got[..., 7], ref[..., 7])
     assert np.array_equal(got[..., 0], ref[..., 0])
-    np.testing.assert_allclose(got[..., 1:5], ref[..., 1:5], rtol=1e-12, atol=1e-12)
-    assert got[..., 5].sum() + counts[:3].sum() == N.size
+    np.testing.assert_allclose(got[..., 1:7], ref[..., 1:7], rtol=1e-12, atol=1e-9)
+    assert got[..., 7].sum() + counts[:3].sum() == N.size
+    # the shifted moments give the bin's mean and variance of ln w
+    fin = np.isfinite(N) & (N > 1.0) & (N <= 4.0)
+    if n_sub == 1:
+        b = int(np.argmax(got[0, :, 7]))
+        sel = fin & (np.digitize(N, np.linspace(1.0, 4.0, 41), right=True) - 1 == b)
+        n = got[0, b, 7]
+        assert math.isclose(got[0, b, 0] + got[0, b, 3] / n, lw[sel].mean(), rel_tol=1e-12)
+        assert math.isclose((got[0, b, 4] - got[0, b, 3] ** 2 / n) / (n - 1), lw[sel].var(ddof=1),
+                            rel_tol=1e-9)
 
 
 def test_histogram_edge_cases():
     bins, counts = oracle.histogram(np.zeros(0), np.zeros(0), 8, 0.0, 1.0)
-    assert counts.tolist() == [0, 0, 0, 0] and np.all(bins[..., 5] == 0)
+    assert counts.tolist() == [0, 0, 0, 0] and np.all(bins[..., 7] == 0)
     assert np.all(bins[..., 0] == -np.inf)
     N = np.array([0.0, 1.0, 1.0 + 1e-15, np.inf, np.nan, -1.0, 0.5])
     lw = np.array([0.1, 0.2, 0.3, 0.4, 0.5, 0.6, -700.0])
     bins, counts = oracle.histogram(N, lw, 2, 0.0, 1.0)
     assert counts.tolist() == [2, 1, 2, 7]
-    assert bins[0, 0, 5] == 1 and bins[0, 1, 5] == 1  # 0.5 -> bin 0 (right-closed), 1.0 -> bin 1
+    assert bins[0, 0, 7] == 1 and bins[0, 1, 7] == 1  # 0.5 -> bin 0 (right-closed), 1.0 -> bin 1
     assert bins[0, 0, 0] == -700.0 and bins[0, 0, 1] == 1.0
     # edges that are exact binary fractions: a value on an edge goes to the bin on its left
     e = np.arange(0, 9) / 8.0
     bins, counts = oracle.histogram(e, np.zeros(9), 8, 0.0, 1.0)
-    assert counts.tolist() == [1, 0, 0, 9] and np.all(bins[0, :, 5] == 1)
+    assert counts.tolist() == [1, 0, 0, 9] and np.all(bins[0, :, 7] == 1)
     with pytest.raises(ValueError):
         oracle.histogram(N, lw, 0, 0.0, 1.0)
     with pytest.raises(ValueError):

@@ -39,7 +39,7 @@ def _worker(rank, world, port, out_dir):
     spec = W.SetSpec(**SPEC)
     mine = shard.shard_sets([spec], rank, world)[0]
     N, lw, bins, counts = _run(mine)
-    f, c = shard.allgather_merge(bins[:, :5], bins[:, 5].astype(np.int64))
+    f, c = shard.allgather_merge(bins[:, :7], bins[:, 7].astype(np.int64))
     np.savez(os.path.join(out_dir, f"r{rank}.npz"), N=N, lw=lw, off=mine.traj_offset, f=f, c=c,
              cnt=counts)
     dist.barrier()
@@ -59,10 +59,11 @@ def test_two_gloo_ranks_match_one_process(tmp_path):
     assert np.array_equal(cat_N, N) and np.array_equal(cat_lw, lw)
     for p in parts:
         f, c = p["f"], p["c"]
-        assert np.array_equal(c, bins[:, 5].astype(np.int64))
+        assert np.array_equal(c, bins[:, 7].astype(np.int64))
         assert np.array_equal(f[:, 0], bins[:, 0])
         np.testing.assert_allclose(f[:, 1:3], bins[:, 1:3], rtol=1e-12, atol=0)
-        np.testing.assert_allclose(f[:, 3:5], bins[:, 3:5], rtol=1e-12, atol=1e-12 * np.abs(bins[:, 3:5]).max())
+        for k in range(3, 7):
+            np.testing.assert_allclose(f[:, k], bins[:, k], rtol=1e-9, atol=1e-9 * np.abs(bins[:, k]).max())
     assert sum(int(p["cnt"][3]) for p in parts) == counts[3]
 
 
@@ -80,8 +81,25 @@ def test_shard_ranges_partition_the_ids():
 
 
 def test_merge_handles_empty_bins():
-    f1 = np.array([[-np.inf, 0, 0, 0, 0], [1.0, 2.0, 3.0, 4.0, 5.0]])
-    f2 = np.array([[0.5, 1.0, 1.0, 0.5, 0.25], [-np.inf, 0, 0, 0, 0]])
+    f1 = np.array([[-np.inf, 0, 0, 0, 0, 0, 0], [1.0, 2.0, 3.0, -1.0, 1.0, -1.0, 1.0]])
+    f2 = np.array([[0.5, 1.0, 1.0, 0.0, 0.0, 0.0, 0.0], [-np.inf, 0, 0, 0, 0, 0, 0]])
     f, c = shard.merge_bins([f1, f2], [np.array([0, 2]), np.array([1, 0])])
     assert np.array_equal(c, [1, 2])
     assert f[0, 0] == 0.5 and f[0, 1] == 1.0 and f[1, 1] == 2.0
+    assert np.array_equal(f[0, 3:], [0, 0, 0, 0]) and np.array_equal(f[1, 3:], [-1, 1, -1, 1])
+
+
+def test_merge_recentres_moments():
+    """Two parts with different maxima: the merged moments equal the moments
+    of the pooled sample about the pooled maximum."""
+    rng = np.random.default_rng(4)
+    a, b = rng.normal(-3, 1, 50), rng.normal(1, 2, 70)
+
+    def part(x):
+        m = x.max()
+        y = x - m
+        return np.array([m, np.exp(y).sum(), np.exp(2 * y).sum(), y.sum(), (y ** 2).sum(), (y ** 3).sum(),
+                         (y ** 4).sum()])
+    f, c = shard.merge_bins([part(a)[None], part(b)[None]], [np.array([50]), np.array([70])])
+    np.testing.assert_allclose(f[0], part(np.concatenate([a, b])), rtol=1e-12)
+    assert c[0] == 120
