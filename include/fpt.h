@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define FPT_ABI_VERSION 1
+#define FPT_ABI_VERSION 2 /* 2: fpt_bin carries four moments of ln w; fpt_estimate */
 
 /* return codes */
 #define FPT_OK 0
@@ -139,11 +139,14 @@ typedef struct fpt_set {
 } fpt_set;
 
 /* Weighted-histogram bin (§2.1 Eq. (9), §2.2 Eq. (16)) with max-shifted sums so
- * that weights spanning hundreds of e-folds stay representable:
+ * that weights spanning hundreds of e-folds stay representable.  With
+ * x_i = ln w_i - max_lw <= 0 over the runs i of the bin:
  *   sum_i w_i   = exp(max_lw) * s1,   sum_i w_i^2 = exp(2 max_lw) * s2,
- *   l1 = sum ln w_i, l2 = sum (ln w_i)^2, count = n_j.  Empty bin: max_lw = -inf. */
+ *   l_k = sum_i x_i^k (k = 1..4: the moments of ln w behind the lognormal
+ *   estimator and the normality test of §2.4), count = n_j.
+ * Empty bin: max_lw = -inf, sums 0.  64 bytes. */
 typedef struct fpt_bin {
-    double max_lw, s1, s2, l1, l2;
+    double max_lw, s1, s2, l1, l2, l3, l4;
     int64_t count;
 } fpt_bin;
 
@@ -191,6 +194,38 @@ int fpt_plan_destroy(fpt_plan* plan);
 int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo,
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
+
+/* Per-bin estimates of the first-passage-time density from a histogram
+ * (fpt_estimate).  d = bin width, n_total = runs of the histogram (all of
+ * them: in range, out of range and censored).
+ *   p_direct, se_direct : sum w / (d n_total) (§2.1 Eq. (9), §2.2 Eq. (16)) and
+ *                         sqrt((sum w^2/n_total - (sum w/n_total)^2)/n_total)/d
+ *   p_lognormal         : n_j exp(mean_lw + var_lw/2) / (d n_total) (§2.4 Eqs. (22), (23))
+ *   eps_lo, eps_hi      : p_lognormal |exp(-+a) - 1|, a = sqrt(var/n_j + var^2/(2 n_j - 2)) (Eq. (24))
+ *   mean_lw, var_lw     : sample mean and unbiased sample variance of ln w in the bin
+ *   skew, kurt          : sample skewness sqrt(b1) = m3/m2^1.5 and kurtosis b2 = m4/m2^2
+ *   z_skew, z_kurt      : their normal deviates (D'Agostino 1970; Anscombe and Glynn 1983)
+ *   k2, p_normal        : D'Agostino-Pearson K^2 = z_skew^2 + z_kurt^2 and its chi^2(2)
+ *                         p-value exp(-K^2/2) (the normality test of ln w in §2.4)
+ *   jk_direct, jk_lognormal : jackknife errors (§2.1): the unbiased spread of the
+ *                         n_sub subset estimates (each with its own n_total) / sqrt(n_sub)
+ * Empty bin: both estimates 0, eps 0.  The lognormal estimate needs n_j >= 2,
+ * the normality test n_j >= 8 and var_lw > 0, the jackknife n_sub >= 2 and
+ * every subset's estimate defined; otherwise NaN.  128 bytes. */
+typedef struct fpt_estimate_bin {
+    double count, p_direct, se_direct, p_lognormal, eps_lo, eps_hi, mean_lw, var_lw;
+    double skew, kurt, z_skew, z_kurt, k2, p_normal, jk_direct, jk_lognormal;
+} fpt_estimate_bin;
+
+/* Estimates of one histogram made by fpt_histogram (or one set's histogram of
+ * fpt_simulate_batch, with n_sub = 1): bins[s * n_bins + j] (device, as
+ * written), n_total runs with global ids id_offset .. id_offset + n_total - 1
+ * (run id i belongs to subset i mod n_sub).  Writes out[j], j < n_bins
+ * (device).  Asynchronous on `stream`; argument errors are reported
+ * synchronously (1 <= n_bins, 1 <= n_sub, n_sub * n_bins <= FPT_MAX_HIST_BINS,
+ * lo < hi finite, n_total >= 1). */
+int fpt_estimate(const fpt_bin* bins, int32_t n_bins, int32_t n_sub, double lo, double hi,
+                 int64_t n_total, uint64_t id_offset, fpt_estimate_bin* out, void* stream);
 
 /* One training record of the learned-bias stepper: the MLP inputs at the start
  * of a k_eval-step block of run `run` (its record index in the call's outputs)

@@ -32,6 +32,7 @@ UNITS = {
     "stepper_mlp.cu": [],
     "train.cu": [],
     "plan.cu": [],
+    "estimate.cu": [],
 }
 
 

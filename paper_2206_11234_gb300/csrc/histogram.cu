@@ -1,8 +1,9 @@
 // Weighted histogram of first-passage times (arXiv:2206.11234 §2.1 Eq. (9),
 // §2.2 Eq. (16)), several histograms (one per parameter set) per launch.
 //
-// Per bin: n_j, max ln w, s1 = sum exp(ln w - max), s2 = sum exp(2 (ln w - max)),
-// l1 = sum ln w, l2 = sum (ln w)^2.  Two streaming passes over the 16-byte
+// Per bin: n_j, max ln w and, with x = ln w - max <= 0, s1 = sum exp(x),
+// s2 = sum exp(2 x), l_k = sum x^k for k = 1..4 (the moments of ln w behind the
+// lognormal estimator and normality test of §2.4).  Two streaming passes over the 16-byte
 // records (the data is HBM-resident and read twice; at ~7 TB/s that is well
 // under a millisecond for 10^7 records):
 //   pass 1: classify each record, per-bin max of ln w (shared-memory atomicMax
@@ -29,6 +30,7 @@ __device__ __forceinline__ double ord_value(unsigned long long k) {
 }
 
 constexpr unsigned long long kKeyNegInf = 0x000fffffffffffffull;  // ord_key(-inf)
+constexpr int kSums = 6;  // s1, s2, l1 .. l4 per bin
 
 // 0: in range (bin set), 1: N <= lo, 2: finite N > hi, 3: N not finite
 __device__ __forceinline__ int classify(double N, const HistSeg& h, unsigned long long gid, int& bin) {
@@ -54,6 +56,8 @@ __global__ void hist_init(const HistSeg* __restrict__ segs, int n_segs, fpt_bin*
         o->s2 = 0.0;
         o->l1 = 0.0;
         o->l2 = 0.0;
+        o->l3 = 0.0;
+        o->l4 = 0.0;
         o->count = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -117,11 +121,11 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
 
 __global__ void hist_pass_sum(const double* __restrict__ N, const double* __restrict__ lw,
                               const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins) {
-    extern __shared__ double s_acc[];  // [nb][4] sums, then [nb] counts
+    extern __shared__ double s_acc[];  // [nb][kSums] sums, then [nb] counts
     const HistSeg h = segs[blockIdx.y];
     const int nb = h.n_bins * h.n_sub;
-    unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_acc + 4 * nb);
-    for (int b = threadIdx.x; b < 4 * nb; b += blockDim.x) s_acc[b] = 0.0;
+    unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_acc + kSums * nb);
+    for (int b = threadIdx.x; b < kSums * nb; b += blockDim.x) s_acc[b] = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0ull;
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
@@ -130,18 +134,20 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
          base += stride) {
         const long long i = base + lane;
         int bin = -1;
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        double v[kSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (i < h.n) {
             const long long r = h.first + i;
             if (classify(N[r], h, h.id_offset + (unsigned long long)i, bin) == 0) {
-                const double x = lw[r];
                 const unsigned long long k =
                     (unsigned long long)__double_as_longlong(bins[h.bin0 + bin].max_lw);
-                const double e = exp(x - ord_value(k));
+                const double x = lw[r] - ord_value(k);
+                const double e = exp(x), x2 = x * x;
                 v[0] = e;
                 v[1] = e * e;
                 v[2] = x;
-                v[3] = x * x;
+                v[3] = x2;
+                v[4] = x2 * x;
+                v[5] = x2 * x2;
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, bin);
@@ -149,22 +155,22 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
         if (__all_sync(0xffffffffu, alone)) {
             if (bin >= 0) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) atomicAdd(&s_acc[4 * bin + f], v[f]);
+                for (int f = 0; f < kSums; ++f) atomicAdd(&s_acc[kSums * bin + f], v[f]);
                 atomicAdd(&s_cnt[bin], 1ull);
             }
         } else {
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            double acc[kSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int src = 0; src < 32; ++src) {
                 const bool take = (peers >> src) & 1u;
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
+                for (int f = 0; f < kSums; ++f) {
                     const double y = __shfl_sync(0xffffffffu, v[f], src);
                     if (take) acc[f] += y;
                 }
             }
             if (bin >= 0 && (int)lane == __ffs(peers) - 1) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) atomicAdd(&s_acc[4 * bin + f], acc[f]);
+                for (int f = 0; f < kSums; ++f) atomicAdd(&s_acc[kSums * bin + f], acc[f]);
                 atomicAdd(&s_cnt[bin], (unsigned long long)__popc(peers));
             }
         }
@@ -173,10 +179,12 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         if (s_cnt[b] == 0ull) continue;
         fpt_bin* o = bins + h.bin0 + b;
-        atomicAdd(&o->s1, s_acc[4 * b + 0]);
-        atomicAdd(&o->s2, s_acc[4 * b + 1]);
-        atomicAdd(&o->l1, s_acc[4 * b + 2]);
-        atomicAdd(&o->l2, s_acc[4 * b + 3]);
+        atomicAdd(&o->s1, s_acc[kSums * b + 0]);
+        atomicAdd(&o->s2, s_acc[kSums * b + 1]);
+        atomicAdd(&o->l1, s_acc[kSums * b + 2]);
+        atomicAdd(&o->l2, s_acc[kSums * b + 3]);
+        atomicAdd(&o->l3, s_acc[kSums * b + 4]);
+        atomicAdd(&o->l4, s_acc[kSums * b + 5]);
         atomicAdd(reinterpret_cast<unsigned long long*>(&o->count), s_cnt[b]);
     }
 }
@@ -192,7 +200,7 @@ __global__ void hist_final(const HistSeg* __restrict__ segs, fpt_bin* __restrict
 
 }  // namespace
 
-size_t hist_smem_bytes(int max_nb) { return (size_t)max_nb * (4 * sizeof(double) + 8); }
+size_t hist_smem_bytes(int max_nb) { return (size_t)max_nb * (kSums * sizeof(double) + 8); }
 
 cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long max_n,
                         const double* N, const double* lw, fpt_bin* bins, fpt_hist_counts* counts,

@@ -16,7 +16,7 @@ from . import build as _build
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-FPT_ABI_VERSION = 1
+FPT_ABI_VERSION = 2
 FPT_OK = 0
 FPT_EINVAL = -1
 FPT_ECUDA = -2
@@ -77,7 +77,16 @@ class FptSet(ctypes.Structure):
 
 class FptBin(ctypes.Structure):
     _fields_ = [("max_lw", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double),
-                ("l1", ctypes.c_double), ("l2", ctypes.c_double), ("count", ctypes.c_int64)]
+                ("l1", ctypes.c_double), ("l2", ctypes.c_double), ("l3", ctypes.c_double),
+                ("l4", ctypes.c_double), ("count", ctypes.c_int64)]
+
+
+ESTIMATE_FIELDS = ("count", "p_direct", "se_direct", "p_lognormal", "eps_lo", "eps_hi", "mean_lw", "var_lw",
+                   "skew", "kurt", "z_skew", "z_kurt", "k2", "p_normal", "jk_direct", "jk_lognormal")
+
+
+class FptEstimateBin(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in ESTIMATE_FIELDS]
 
 
 class FptHistCounts(ctypes.Structure):
@@ -97,7 +106,7 @@ class FptMlpTrainStats(ctypes.Structure):
                 ("frac_in_tail", ctypes.c_double), ("n_records", ctypes.c_int64)]
 
 
-BIN_FIELDS = 6  # an fpt_bin is 6 x 8 bytes: view bins as float64[n, 6] (count as int64 bits)
+BIN_FIELDS = 8  # an fpt_bin is 8 x 8 bytes: view bins as float64[n, 8] (count as int64 bits)
 
 
 class FptError(RuntimeError):
@@ -121,6 +130,7 @@ def _load():
     L.fpt_simulate_batch.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
     L.fpt_simulate_batch_host.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
     L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
+    L.fpt_estimate.argtypes = [vp, i32, i32, d, d, i64, u64, vp, vp]
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -267,6 +277,16 @@ def fpt_histogram(N: torch.Tensor, logw: torch.Tensor, n_bins: int, lo: float, h
                              lo, hi, n_sub, id_offset, _dptr(bins), _dptr(counts), _stream(stream)))
 
 
+def fpt_estimate(bins: torch.Tensor, n_bins: int, lo: float, hi: float, n_total: int, out: torch.Tensor,
+                 n_sub: int = 1, id_offset: int = 0, stream=None):
+    """Per-bin estimates (fpt_estimate_bin, viewed as float64[n_bins, 16]) of a
+    histogram of n_total runs; `bins` as written by fpt_histogram."""
+    if out.dtype != torch.float64 or out.numel() < 16 * n_bins:
+        raise ValueError("out must be float64 with 16 values per bin")
+    _check(lib.fpt_estimate(_dptr(bins), n_bins, n_sub, lo, hi, n_total, id_offset, _dptr(out),
+                            _stream(stream)))
+
+
 def fpt_normals(seed: int, traj: int, set_id: int, k0: int, n_blocks: int, precision, out: torch.Tensor,
                 stream=None):
     prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
@@ -390,11 +410,30 @@ def empty_counts(n: int = 1, device="cuda") -> torch.Tensor:
 
 
 def bins_to_numpy(bins: torch.Tensor):
-    """(fields float64[n, 5], count int64[n]) from an fpt_bin array."""
+    """(fields float64[n, 7], count int64[n]) from an fpt_bin array."""
     b = bins.detach().cpu().contiguous()
-    f = b.numpy()[:, :5].copy()
-    c = b.view(torch.int64).numpy()[:, 5].copy()
+    f = b.numpy()[:, :7].copy()
+    c = b.view(torch.int64).numpy()[:, 7].copy()
     return f, c
+
+
+def empty_estimates(n_bins: int, device="cuda") -> torch.Tensor:
+    return torch.empty((n_bins, len(ESTIMATE_FIELDS)), dtype=torch.float64, device=device)
+
+
+def estimates_to_dict(est: torch.Tensor) -> dict:
+    """{field: float64 numpy array [n_bins]} from fpt_estimate's output."""
+    a = est.detach().cpu().numpy()
+    return {f: a[:, i].copy() for i, f in enumerate(ESTIMATE_FIELDS)}
+
+
+def lognormal_applies(est: dict, threshold: float = 0.005, min_count: int = 8) -> bool:
+    """The rule of §2.4: the lognormal estimate is used when no bin's normality
+    p-value (bins with >= min_count runs) falls below the threshold (0.5 %)."""
+    import numpy as np
+    p = est["p_normal"][est["count"] >= min_count]
+    p = p[np.isfinite(p)]
+    return bool(np.all(p >= threshold))
 
 
 def simulate_workload(workload, *, block_dim=0, k_steps=0, device="cuda", with_hist=True, stream=None,

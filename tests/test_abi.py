@@ -38,7 +38,7 @@ def test_struct_layouts_match_header(native, tmp_path):
     the header's structs."""
     structs = {"fpt_params": native.FptParams, "fpt_set": native.FptSet, "fpt_bin": native.FptBin,
                "fpt_hist_counts": native.FptHistCounts, "fpt_mlp_train_state": native.FptMlpTrainState,
-               "fpt_mlp_train_stats": native.FptMlpTrainStats}
+               "fpt_mlp_train_stats": native.FptMlpTrainStats, "fpt_estimate_bin": native.FptEstimateBin}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fpt.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -120,6 +120,15 @@ def test_host_side_argument_checks(native):
     assert h(8, 1024, 0.0, 1.0, 5) == E
     assert h(8, 8, 0.0, 1.0, 0) == E
     assert L.fpt_histogram(None, buf, 8, 8, 0.0, 1.0, 1, 0, buf, buf, None) == E
+    # estimates of a histogram
+    est = lambda nb, ns, lo, hi, n: L.fpt_estimate(buf, nb, ns, lo, hi, n, 0, buf, None)
+    assert est(0, 1, 0.0, 1.0, 10) == E
+    assert est(8, 0, 0.0, 1.0, 10) == E
+    assert est(1024, 5, 0.0, 1.0, 10) == E
+    assert est(8, 1, 1.0, 0.0, 10) == E
+    assert est(8, 1, 0.0, math.nan, 10) == E
+    assert est(8, 1, 0.0, 1.0, 0) == E
+    assert L.fpt_estimate(None, 8, 1, 0.0, 1.0, 10, 0, buf, None) == E
     # batch
     sets = (native.FptSet * 2)()
     for s in sets:

@@ -1,0 +1,126 @@
+"""GPU per-bin estimators (fpt_histogram -> fpt_estimate, from per-bin sums)
+against the oracle's estimators computed from the raw records (§2.1 Eq. (9),
+§2.2 Eq. (16), §2.4 Eqs. (22)-(24), the D'Agostino-Pearson test of §2.4, the
+jackknife of §2.1).
+
+Tolerances: both sides are binary64.  The GPU forms central moments from
+moments about the bin maximum after merging subsets; the oracle centres the
+samples first.  The re-centring amplifies rounding by at most (spread / sd)^k
+for the k-th moment (spread = max - mean, a few sd here), so quantities built
+from the first two moments agree to ~1e-12 and skewness / kurtosis statistics
+to ~1e-9; the tests allow 1e-9 and 1e-7 respectively.  A wrong subset total,
+a dropped re-centring term or a transposed moment index shows up at O(1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import estimate as OE
+from paper_2206_11234_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = ("p_direct", "se_direct", "p_lognormal", "eps_lo", "eps_hi", "mean_lw", "var_lw", "jk_direct",
+         "jk_lognormal")
+STATS = ("skew", "kurt", "z_skew", "z_kurt", "k2")
+
+
+@pytest.fixture(scope="module")
+def nat(cuda_device):
+    from paper_2206_11234_gb300 import native
+    return native
+
+
+def _gpu_estimate(nat, N, lw, n_bins, lo, hi, n_sub=1, id_offset=0):
+    import torch
+    tN = torch.from_numpy(np.ascontiguousarray(N, dtype=np.float64)).cuda()
+    tl = torch.from_numpy(np.ascontiguousarray(lw, dtype=np.float64)).cuda()
+    bins = nat.empty_bins(n_bins * n_sub)
+    counts = nat.empty_counts(1)
+    nat.fpt_histogram(tN, tl, n_bins, lo, hi, bins, counts, n_sub=n_sub, id_offset=id_offset)
+    est = nat.empty_estimates(n_bins)
+    nat.fpt_estimate(bins, n_bins, lo, hi, len(N), est, n_sub=n_sub, id_offset=id_offset)
+    return nat.estimates_to_dict(est)
+
+
+def _compare(got, ref):
+    np.testing.assert_array_equal(got["count"], ref["count"])
+    for f in ref:
+        assert np.array_equal(np.isnan(got[f]), np.isnan(ref[f])), f
+    for f in TIGHT:
+        np.testing.assert_allclose(got[f], ref[f], rtol=1e-9, atol=1e-300, equal_nan=True, err_msg=f)
+    for f in STATS:
+        np.testing.assert_allclose(got[f], ref[f], rtol=1e-7, atol=1e-7, equal_nan=True, err_msg=f)
+    ok = np.isfinite(ref["p_normal"]) & (ref["p_normal"] > 1e-200)
+    np.testing.assert_allclose(got["p_normal"][ok], ref["p_normal"][ok], rtol=1e-5)
+
+
+def _drift_like_records(n, seed, lo, hi):
+    """ln w correlated with N plus skewed noise, a few runs out of range or censored."""
+    rng = np.random.default_rng(seed)
+    N = rng.normal(0.5 * (lo + hi), 0.2 * (hi - lo), n)
+    N[rng.random(n) < 0.01] = np.inf
+    lw = -30.0 - 4.0 * (N - lo) + 0.8 * rng.standard_normal(n) + 0.3 * rng.exponential(1.0, n)
+    lw[~np.isfinite(N)] = -1.0
+    return N, lw
+
+
+@pytest.mark.parametrize("n,n_bins,n_sub,id_offset", [(1, 5, 1, 0), (50, 4, 3, 7), (20000, 40, 1, 0),
+                                                      (100003, 100, 16, 5), (300000, 256, 12, 123456789)])
+def test_estimates_match_oracle(nat, n, n_bins, n_sub, id_offset):
+    N, lw = _drift_like_records(n, seed=n, lo=7.0, hi=10.0)
+    got = _gpu_estimate(nat, N, lw, n_bins, 7.0, 10.0, n_sub, id_offset)
+    ref = OE.estimate(N, lw, n_bins, 7.0, 10.0, n_sub=n_sub, id_offset=id_offset)
+    _compare(got, ref)
+
+
+def test_estimates_wide_log_weights_and_unit_weights(nat):
+    # ln w spread over tens of e-folds inside a bin (random_records), and w = 1
+    N, lw = W.random_records(150000, seed=9, lo=0.0, hi=6.0)
+    _compare(_gpu_estimate(nat, N, lw, 60, 0.0, 6.0, 10, 3), OE.estimate(N, lw, 60, 0.0, 6.0, n_sub=10, id_offset=3))
+    z = np.zeros_like(lw)
+    got = _gpu_estimate(nat, N, z, 60, 0.0, 6.0)
+    _compare(got, OE.estimate(N, z, 60, 0.0, 6.0))
+    ok = got["count"] >= 2
+    np.testing.assert_array_equal(got["p_lognormal"][ok], got["p_direct"][ok])
+
+
+def test_estimate_rejects_bad_arguments(nat):
+    bins = nat.empty_bins(8)
+    est = nat.empty_estimates(8)
+    for args in ((0, 0.0, 1.0, 10, 1), (8, 1.0, 0.0, 10, 1), (8, 0.0, 1.0, 0, 1), (8, 0.0, 1.0, 10, 0),
+                 (1024, 0.0, 1.0, 10, 5)):
+        with pytest.raises(nat.FptError) as ei:
+            nat.fpt_estimate(bins, args[0], args[1], args[2], args[3], est if args[0] <= 8 else
+                             nat.empty_estimates(args[0]), n_sub=args[4])
+        assert ei.value.code == nat.FPT_EINVAL
+
+
+def test_lognormal_rule_on_simulated_runs(nat):
+    """The §2.4 workflow on the GPU path: drift-dominated runs (m = 0.01, b = 1)
+    have lognormal weights within a bin, and there the lognormal and the
+    direct estimates agree within their errors; diffusion-dominated runs
+    (m = 1, wall at 9, b = 0.4) fail the normality test by far."""
+    import torch
+    spec = W.SetSpec(phi_in=6.0, m=0.01, b=1.0, dN=1e-3, n_max=10.0, n_traj=1 << 20, hist_lo=8.45,
+                     hist_hi=8.75, n_bins=30)
+    wl = W.Workload("drift b=1", [spec], "f32_f64acc", seed=4)
+    N, lw, _, _ = nat.simulate_workload(wl, with_hist=False)
+    got = _gpu_estimate(nat, N.cpu().numpy(), lw.cpu().numpy(), spec.n_bins, spec.hist_lo, spec.hist_hi, 16, 0)
+    big = got["count"] >= 400
+    assert big.sum() >= 10
+    p = got["p_normal"][big]
+    assert np.median(p) > 0.05 and np.mean(p < 0.005) <= 0.1, p
+    d = np.abs(got["p_lognormal"][big] - got["p_direct"][big])
+    err = np.hypot(np.maximum(got["eps_lo"][big], got["eps_hi"][big]), got["se_direct"][big])
+    assert np.mean(d <= 3 * err) >= 0.9
+    spec = W.SetSpec(phi_in=8.0, m=1.0, b=0.4, dN=5e-4, n_max=60.0, phi_uv=9.0, n_traj=1 << 20, hist_lo=0.0,
+                     hist_hi=60.0, n_bins=60)
+    wl = W.Workload("diffusion b=0.4", [spec], "f32_f64acc", seed=4)
+    N, lw, _, _ = nat.simulate_workload(wl, with_hist=False)
+    got = _gpu_estimate(nat, N.cpu().numpy(), lw.cpu().numpy(), spec.n_bins, spec.hist_lo, spec.hist_hi)
+    big = got["count"] >= 400
+    assert big.sum() >= 20
+    assert np.median(got["p_normal"][big]) < 1e-10
+    assert not nat.lognormal_applies(got)
