@@ -11,7 +11,10 @@ Parity status of each function (what pins it is listed in the tests):
   normals4           pinned: normal-distribution KS and moment tests
   simulate           pinned: inverse-Gaussian law (constant model), <N> and
                      Var N from the backward equations, E[w] = 1, log w = 0 at
-                     b = 0, the brute-force path likelihood ratio
+                     b = 0, the brute-force path likelihood ratio; power-law
+                     bias (§3.5 Eq. (26)): p = 1 equals the constant bias,
+                     path likelihood ratio for p = 0, 2.5, 3, backward-equation
+                     mean with drift D + A phi^3, E[w] = 1, classical duration
   histogram          pinned: brute-force binning with numpy.digitize; moments
                      of ln w - max_lw against numpy mean / var
   estimate (module)  pinned: scipy.stats normaltest / skewtest / kurtosistest;
@@ -32,6 +35,7 @@ from . import build as _build
 MODEL_QUADRATIC = 0
 MODEL_CONSTANT = 1
 BIAS_CONST = 0
+BIAS_POWER = 1
 BIAS_MLP = 2
 MLP_HIDDEN = 64
 MLP_NPARAM = 64 * 2 + 64 + 64 * 64 + 64 + 64 + 1
@@ -56,6 +60,7 @@ class OracleRun(ctypes.Structure):
         ("mlp", ctypes.POINTER(ctypes.c_double)),
         ("mlp_norm", ctypes.c_double * 4),
         ("k_eval", ctypes.c_int32),
+        ("bias_p", ctypes.c_double),
     ]
 
 
@@ -94,7 +99,9 @@ def _ptr(a, ct):
 
 def make_run(*, model=MODEL_QUADRATIC, m=1.0, a0=0.0, s0=0.0, phi_in, phi_end=math.sqrt(2.0),
              phi_uv=math.inf, dN, b=0.0, n_max, seed=0, set_id=0, traj_offset=0, mlp=None,
-             mlp_norm=(0.0, 1.0, 0.0, 1.0), k_eval=1):
+             mlp_norm=(0.0, 1.0, 0.0, 1.0), k_eval=1, bias_p=None):
+    """One parameter set.  b is the amplitude of B = b S(phi), or, with bias_p
+    given, of the power law B = b phi^bias_p (§3.5 Eq. (26))."""
     r = OracleRun()
     r.model, r.m, r.a0, r.s0 = model, m, a0, s0
     r.phi_in, r.phi_end, r.phi_uv = phi_in, phi_end, phi_uv
@@ -103,6 +110,9 @@ def make_run(*, model=MODEL_QUADRATIC, m=1.0, a0=0.0, s0=0.0, phi_in, phi_end=ma
     r.bias_kind = BIAS_CONST
     r.mlp_norm = (ctypes.c_double * 4)(*mlp_norm)
     r.k_eval = k_eval
+    if bias_p is not None:
+        r.bias_kind = BIAS_POWER
+        r.bias_p = bias_p
     if mlp is not None:
         arr = np.ascontiguousarray(mlp, dtype=np.float64)
         assert arr.size == MLP_NPARAM

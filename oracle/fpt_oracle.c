@@ -164,6 +164,8 @@ static int run_valid(const oracle_run* r) {
     }
     if (r->bias_kind == ORACLE_BIAS_MLP) {
         if (r->mlp == NULL || r->k_eval < 1) return 0;
+    } else if (r->bias_kind == ORACLE_BIAS_POWER) {
+        if (r->model != ORACLE_MODEL_QUADRATIC || !isfinite(r->bias_p)) return 0;
     } else if (r->bias_kind != ORACLE_BIAS_CONST) {
         return 0;
     }
@@ -219,7 +221,8 @@ static int64_t run_one(const oracle_run* r, uint64_t traj, double* N_out, double
         blk_xisum += xi;
         const double D = drift(r, phi);
         const double S = noise(r, phi);
-        const double B = b_cur * S; /* §2.3 Eq. (18) with f = S */
+        /* §2.3 Eq. (18) with f = S, or the power law of §3.5 Eq. (26) */
+        const double B = r->bias_kind == ORACLE_BIAS_POWER ? r->b * pow(phi, r->bias_p) : b_cur * S;
         /* §2.2 Eq. (11): x_{m+1} - x_m = [D + B] dt + S xi sqrt(dt) */
         double phi_new = phi + (D + B) * dN + S * xi * sq;
         /* log of §2.2 Eq. (12) with the step densities of Eqs. (13)-(14):
@@ -227,7 +230,7 @@ static int64_t run_one(const oracle_run* r, uint64_t traj, double* N_out, double
          * the opposite overall sign; expanding (13)/(14) gives this one.) */
         lw -= (B / (S * S)) * (0.5 * B * dN + S * xi * sq);
         if (rec && rec->xi) rec->xi[m] = xi;
-        if (rec && rec->b_used) rec->b_used[m] = b_cur;
+        if (rec && rec->b_used) rec->b_used[m] = B / S;
         /* Reflecting wall at phi_UV (§2.3 below Eq. (19), §3): mirror once. */
         if (phi_new > r->phi_uv) phi_new = 2.0 * r->phi_uv - phi_new;
         if (rec && rec->phi) rec->phi[m + 1] = phi_new;

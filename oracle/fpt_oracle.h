@@ -26,9 +26,10 @@ extern "C" {
 #define ORACLE_MODEL_QUADRATIC 0 /* §3 Eq. (25) with §2.3 Eq. (17): D = -2/phi, S = m phi / (2 pi sqrt 6) */
 #define ORACLE_MODEL_CONSTANT 1  /* test model: D = a0, S = s0 (constant drift and noise) */
 
-/* Bias kinds (§2.3 Eq. (18): B = A f(phi); here B = b(.) * S(phi)). */
-#define ORACLE_BIAS_CONST 0 /* b constant: f = S, A = b */
-#define ORACLE_BIAS_MLP 2   /* b = MLP(phi, N_elapsed), re-evaluated every k_eval steps */
+/* Bias kinds (§2.3 Eq. (18): B = A f(phi)). */
+#define ORACLE_BIAS_CONST 0 /* B = b S(phi): f = S, A = b */
+#define ORACLE_BIAS_POWER 1 /* B = b phi^p (§3.5 Eq. (26)): A_p = b, p = bias_p */
+#define ORACLE_BIAS_MLP 2   /* B = b(phi, N_elapsed) S(phi), b an MLP re-evaluated every k_eval steps */
 
 #define ORACLE_MLP_HIDDEN 64
 /* Parameter vector layout: W1[64][2], b1[64], W2[64][64], b2[64], w3[64], b3[1]. */
@@ -50,6 +51,8 @@ typedef struct {
     const double* mlp;  /* ORACLE_MLP_NPARAM parameters */
     double mlp_norm[4]; /* inputs: x0 = (phi - c0) * s0, x1 = (N - c1) * s1 as {c0, s0, c1, s1} */
     int32_t k_eval;     /* bias is re-evaluated at steps m = 0, k_eval, 2 k_eval, ... */
+    /* power-law bias only */
+    double bias_p;      /* exponent p of B = b phi^p */
 } oracle_run;
 
 /* Philox4x32-10 block function: out = Philox(ctr, key), 10 rounds. */
@@ -67,7 +70,7 @@ int oracle_simulate(const oracle_run* run, int64_t n, double* out_N, double* out
                     int64_t* out_steps);
 
 /* One run, recording the path: phi[0..M] (M+1 values, at most max_steps+1),
- * the normals xi[0..M-1] and the bias amplitude b_used[0..M-1] of each step.
+ * the normals xi[0..M-1] and the bias amplitude b_used[0..M-1] = B/S of each step.
  * Returns M, or -1 if the run needs more than max_steps steps. */
 int64_t oracle_path(const oracle_run* run, int64_t index, int64_t max_steps, double* phi,
                     double* xi, double* b_used, double* out_N, double* out_logw);

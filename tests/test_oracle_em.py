@@ -232,3 +232,63 @@ def test_biased_and_direct_histograms_agree():
         assert abs(p0 - p1) < 4 * math.hypot(s0, s1), j
         compared += 1
     assert compared >= 8
+
+
+# ---- power-law bias B = A_p phi^p (§3.5 Eq. (26)) ----
+
+C0 = 1.0 / (2.0 * math.pi * math.sqrt(6.0))
+
+
+def test_power_bias_p1_is_the_constant_bias():
+    """p = 1 with A_1 = b c0 m is the bias B = b S of §2.3 Eq. (18)."""
+    r1 = oracle.make_run(m=1.0, phi_in=3.0, phi_uv=3.5, dN=1e-3, b=0.8, n_max=6.0)
+    r2 = oracle.make_run(m=1.0, phi_in=3.0, phi_uv=3.5, dN=1e-3, b=0.8 * C0, n_max=6.0, bias_p=1.0)
+    a, b = oracle.simulate(r1, 300), oracle.simulate(r2, 300)
+    assert np.array_equal(a[2], b[2])
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-13)
+    np.testing.assert_allclose(b[1], a[1], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("p,amp", [(3.0, 0.004), (2.5, 0.01), (0.0, 0.3)])
+def test_power_bias_weight_is_the_path_likelihood_ratio(p, amp):
+    """ln w of a state-dependent bias equals ln p_T - ln p_S from the Gaussian
+    step densities of Eqs. (13)-(14), step by step (brute force)."""
+    dN = 1e-3
+    r = oracle.make_run(m=1.0, phi_in=3.0, phi_uv=4.0, dN=dN, b=amp, n_max=20.0, bias_p=p)
+    D, S = _quad_fns(1.0)
+    for i in range(3):
+        phi, xi, bu, Ni, lwi = oracle.path(r, i, 400000)
+        np.testing.assert_allclose(bu * S(phi[:-1]), amp * phi[:-1] ** p, rtol=1e-13)
+        ref = A.path_log_likelihood_ratio(phi, bu, D, S, dN)
+        assert abs(lwi - ref) < 1e-8 * (1 + abs(ref)) + 1e-9 * xi.size
+
+
+def test_power_bias_means_and_unit_mean_weight():
+    """Sample-process mean FPT from the backward equation with drift D + A phi^3
+    (wall at 4), E[w] = 1, and the weighted mean equal to the b = 0 value."""
+    n, dN, amp, p = 6000, 1e-3, 0.004, 3.0
+    r = oracle.make_run(m=1.0, phi_in=3.0, phi_uv=4.0, dN=dN, b=amp, n_max=200.0, bias_p=p)
+    N, lw, _ = oracle.simulate(r, n)
+    assert np.all(np.isfinite(N))
+    Ds = lambda x: A.quad_drift(x, 0.0, 1.0) + amp * x ** p
+    S = lambda x: A.quad_noise(x, 1.0)
+    ms, vs = A.backward_moments_fd(3.0, Ds, S, SQ2, 4.0)
+    assert abs(N.mean() - ms) < 4 * math.sqrt(vs / n) + 2e-3
+    w = np.exp(lw)
+    assert abs(w.mean() - 1.0) < 4 * w.std() / math.sqrt(n)
+    mt = A.mean_fpt_quad(3.0, 1.0, b=0.0, phi_uv=4.0)
+    est = np.sum(w * N) / np.sum(w)
+    se = math.sqrt(np.mean((w * (N - est)) ** 2) / n) / np.mean(w)
+    assert abs(est - mt) < 4 * se + 2e-3
+
+
+def test_power_bias_drift_dominated_classical_duration():
+    """m = 0.01: the sample duration approaches the classical
+    N_S,cl = int dphi / (2/phi - A_p phi^p) from phi_end to phi_in (§2.4)."""
+    from scipy import integrate
+    p, amp, dN = 3.0, 1e-4, 1e-3  # drift stays negative: amp < 2 / phi_in^(p+1)
+    r = oracle.make_run(m=0.01, phi_in=6.0, dN=dN, b=amp, n_max=20.0, bias_p=p)
+    N, lw, _ = oracle.simulate(r, 400)
+    ncl = integrate.quad(lambda x: 1.0 / (2.0 / x - amp * x ** p), SQ2, 6.0, epsabs=1e-12, epsrel=1e-12)[0]
+    assert ncl > 8.6  # the bias lengthens inflation by several sigma_N ~ 0.02
+    assert abs(N.mean() / ncl - 1) < 5e-4
