@@ -230,7 +230,7 @@ static int64_t run_one(const oracle_run* r, uint64_t traj, double* N_out, double
          * the opposite overall sign; expanding (13)/(14) gives this one.) */
         lw -= (B / (S * S)) * (0.5 * B * dN + S * xi * sq);
         if (rec && rec->xi) rec->xi[m] = xi;
-        if (rec && rec->b_used) rec->b_used[m] = B / S;
+        if (rec && rec->b_used) rec->b_used[m] = r->bias_kind == ORACLE_BIAS_POWER ? B / S : b_cur;
         /* Reflecting wall at phi_UV (§2.3 below Eq. (19), §3): mirror once. */
         if (phi_new > r->phi_uv) phi_new = 2.0 * r->phi_uv - phi_new;
         if (rec && rec->phi) rec->phi[m + 1] = phi_new;
