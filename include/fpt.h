@@ -71,9 +71,10 @@ extern "C" {
 #define FPT_PREC_F32_KAHAN 1  /* binary32 state; ln w from binary32 block sums + compensated (Kahan) running sum */
 #define FPT_PREC_F32_F64ACC 2 /* binary32 state; ln w running sum and crossing interpolation in binary64 */
 
-/* bias B = b S */
-#define FPT_BIAS_CONST 0 /* b constant */
-#define FPT_BIAS_MLP 2   /* b = MLP(phi, N_elapsed), held for k_eval steps (see fpt_mlp_params) */
+/* bias of the sample process (§2.3 Eq. (18)) */
+#define FPT_BIAS_CONST 0 /* B = b S(phi), b constant (the set's bias) */
+#define FPT_BIAS_POWER 1 /* B = A_p phi^p (§3.5 Eq. (26)), A_p = the set's bias, p = bias_p; quadratic model */
+#define FPT_BIAS_MLP 2   /* B = b S, b = MLP(phi, N_elapsed), held for k_eval steps (see fpt_mlp_params) */
 
 #define FPT_MAX_SETS 64       /* parameter sets per batched launch */
 #define FPT_MAX_HIST_BINS 4096 /* n_sub * n_bins per histogram */
@@ -86,6 +87,7 @@ typedef struct fpt_params {
     double m;            /* inflaton mass (quadratic model), > 0 */
     double a0, s0;       /* constant model: drift and noise amplitude (s0 > 0) */
     double n_max;        /* censoring time, finite and > 0 */
+    double bias_p;       /* FPT_BIAS_POWER: exponent p (finite; integers 0..4 have specialised kernels) */
     const void* mlp;     /* FPT_BIAS_MLP: device pointer to an fpt_mlp_params */
     int32_t k_eval;      /* FPT_BIAS_MLP: steps between bias evaluations (0 = 32) */
     int32_t block_dim;   /* threads per block of the stepper (0 = autotuned or default) */
@@ -117,7 +119,7 @@ typedef struct fpt_mlp_params {
  *   phi_in, phi_end : start and end of inflation; phi_in <= phi_end gives N = 0, ln w = 0
  *   phi_uv          : reflecting wall, >= phi_in, or +INFINITY for none
  *   dN              : time step (e-folds), > 0
- *   bias            : b (FPT_BIAS_CONST), ignored for FPT_BIAS_MLP
+ *   bias            : b (FPT_BIAS_CONST), A_p (FPT_BIAS_POWER), ignored for FPT_BIAS_MLP
  *   out_N, out_logw : device double[n_traj]; out_N[i] = +inf when censored.
  * n_traj = 0 is a no-op.  Errors: FPT_EINVAL, FPT_EUNSUPPORTED, FPT_ECUDA,
  * FPT_ENOMEM, FPT_EDEVICE_STATUS. */

@@ -24,6 +24,7 @@ UNITS = {
     "abi.cu": [],
     "histogram.cu": [],
     "stepper_f32.cu": [],
+    "stepper_pow.cu": [],
     "stepper_f64.cu": ["-fmad=false", "-DFPT_STEPPER_MAXNREG=128"],
     "rng_probe.cu": ["-fmad=false"],
     "noalloc.cu": [],

@@ -66,10 +66,16 @@ int check_params(const fpt_params* p) {
     if (p->precision != FPT_PREC_F64 && p->precision != FPT_PREC_F32_KAHAN &&
         p->precision != FPT_PREC_F32_F64ACC)
         return fail(FPT_EINVAL, "unknown precision %d", p->precision);
-    if (p->bias_kind != FPT_BIAS_CONST && p->bias_kind != FPT_BIAS_MLP)
+    if (p->bias_kind != FPT_BIAS_CONST && p->bias_kind != FPT_BIAS_POWER && p->bias_kind != FPT_BIAS_MLP)
         return fail(FPT_EINVAL, "unknown bias_kind %d", p->bias_kind);
     if (p->bias_kind == FPT_BIAS_MLP)
         return fail(FPT_EUNSUPPORTED, "the learned bias runs through fpt_simulate_mlp");
+    if (p->bias_kind == FPT_BIAS_POWER) {
+        if (p->model != FPT_MODEL_QUADRATIC)
+            return fail(FPT_EUNSUPPORTED, "the power-law bias is defined for the quadratic model");
+        if (!std::isfinite(p->bias_p) || std::fabs(p->bias_p) > 64.0)
+            return fail(FPT_EINVAL, "bias_p %g must be finite with |p| <= 64", p->bias_p);
+    }
     if (p->model == FPT_MODEL_CONSTANT && !(p->s0 > 0.0 && std::isfinite(p->s0) && std::isfinite(p->a0)))
         return fail(FPT_EINVAL, "constant model needs finite a0 and s0 > 0");
     if (p->block_dim != 0 && (p->block_dim < 32 || p->block_dim > kStepperMaxThreads || p->block_dim % 32))
@@ -118,7 +124,17 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
     // binary32 step constants; the noise coefficient carries -sqrt(2 ln 2), the
     // factor between the stepper's Box–Muller radius rho and the normal (rng.cuh)
     const double neg_sqrt2ln2 = -1.1774100225154747;
-    if (p->model == FPT_MODEL_QUADRATIC) {
+    if (p->bias_kind == FPT_BIAS_POWER) {
+        // B = A_p phi^p: dphi/phi = A_p dN phi^(p-1) + c m sqrt(dN) xi - 2 dN / phi^2;
+        // the step's log-weight is -beta sqrt(dN) xi - beta^2 dN / 2 with beta = B/S = (A_p/c m) phi^(p-1)
+        c.pw = p->bias_p;
+        c.f_c1 = (float)(s.b * s.dN);                        // A_p dN, times phi^(p-1)
+        c.f_c2 = (float)(neg_sqrt2ln2 * c.cm * c.sq);
+        c.f_c3 = (float)(-2.0 * s.dN);
+        c.f_pm1 = (float)(p->bias_p - 1.0);
+        c.f_pw1 = (float)(-s.b / (c.cm * c.cm));
+        c.f_pw2 = (float)(-0.5 * s.b * s.b * s.dN / (c.cm * c.cm));
+    } else if (p->model == FPT_MODEL_QUADRATIC) {
         c.f_c1 = (float)(s.b * c.cm * s.dN);                 // bias part of dphi/phi
         c.f_c2 = (float)(neg_sqrt2ln2 * c.cm * c.sq);        // noise part of dphi/phi per unit rho cos
         c.f_c3 = (float)(-2.0 * s.dN);                       // drift part of dphi, times phi
@@ -181,6 +197,17 @@ int prepare(const fpt_params* p, const fpt_set* sets, int n_sets, bool with_hist
 int pick_stepper(const fpt_params* p, bool wall, StepperKernel* k, int* block) {
     int b = p->block_dim;
     int s = p->k_steps;
+    if (p->bias_kind == FPT_BIAS_POWER) {
+        if (b == 0) b = 256;
+        if (p->precision == FPT_PREC_F64) {
+            *k = stepper_f64(kModelPowReal, wall, s == 0 ? 4 : s);
+        } else {
+            *k = stepper_f32_pow(p->precision, p->bias_p, wall, s == 0 ? 32 : s);
+        }
+        if (!k->func) return fail(FPT_EINVAL, "k_steps %d not available for the power-law bias", s);
+        *block = b;
+        return FPT_OK;
+    }
     if (b == 0 || s == 0) {
         int tb = 0, ts = 0;
         if (tuned_shape(p->precision, p->model, wall, &tb, &ts)) {

@@ -20,7 +20,9 @@
 // with B = b S the step term is -(b xi sqrt(dN) + b^2 dN / 2), so a run of M
 // steps has ln w = -b sqrt(dN) W - b^2 M dN / 2 with W = sum xi.  W is summed
 // per block in the state precision and folded into a running sum that is
-// either compensated binary32 (Kahan) or binary64.
+// either compensated binary32 (Kahan) or binary64.  With the power-law bias
+// B = A_p phi^p (§3.5 Eq. (26)) the amplitude B/S changes every step, so the
+// power models sum the step log-weights themselves instead of the normals.
 #pragma once
 #include <cstdint>
 
@@ -34,6 +36,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 
 // ---------------------------------------------------------------------------
 // Model steps.  phi' = phi + (D + b S) dN + S xi sqrt(dN)   (§2.2 Eq. (11))
@@ -74,6 +87,65 @@ struct ModelStep<float, FPT_MODEL_CONSTANT> {
     }
     __device__ __forceinline__ float step(float phi, float t) const { return __fadd_rn(phi, t); }
 };
+
+// Quadratic potential with B = A_p phi^p, binary32.  With u = phi^(p-1):
+// dphi = phi t - 2 dN / phi, t = A_p dN u + c m sqrt(dN) xi, and the step's
+// log-weight -beta sqrt(dN) xi - beta^2 dN / 2 with beta = B/S = (A_p / c m) u,
+// i.e. u (a1 g + a2 u) with g = c m sqrt(dN) xi, a1 = -A_p/(c m)^2 and
+// a2 = -A_p^2 dN / (2 (c m)^2).  g is formed from a Box–Muller pair as
+// (kq rho) trig, like the constant-bias step.
+template <int MODEL>
+struct ModelStep<float, MODEL> {
+    static_assert(is_pow_model(MODEL), "binary32 model tag");
+    float tc, kq, m2dN, a1, a2, pm1;
+    __device__ __forceinline__ void load(const SetConst& s) {
+        tc = s.f_c1;
+        kq = s.f_c2;
+        m2dN = s.f_c3;
+        a1 = s.f_pw1;
+        a2 = s.f_pw2;
+        pm1 = s.f_pm1;
+    }
+    __device__ __forceinline__ float u_of(float phi, float inv) const {
+        constexpr int p = MODEL - kModelPow;
+        if constexpr (p == 0) return inv;
+        else if constexpr (p == 1) return 1.0f;
+        else if constexpr (p == 2) return phi;
+        else if constexpr (p == 3) return __fmul_rn(phi, phi);
+        else if constexpr (p == 4) return __fmul_rn(__fmul_rn(phi, phi), phi);
+        else return ex2_approx(__fmul_rn(pm1, lg2_approx(phi)));
+    }
+    // one step from phi with noise factor q trig; adds the step's log-weight to acc
+    __device__ __forceinline__ float advance(float phi, float q, float trig, float& acc) const {
+        const float inv = rcp_approx(phi);
+        const float u = u_of(phi, inv);
+        const float g = __fmul_rn(q, trig);
+        const float t = __fmaf_rn(tc, u, g);
+        acc = __fmaf_rn(u, __fmaf_rn(a2, u, __fmul_rn(a1, g)), acc);
+        return __fadd_rn(phi, __fmaf_rn(phi, t, __fmul_rn(m2dN, inv)));
+    }
+};
+
+// Four binary32 EM steps of a power model: as steps4_f32, with the block's
+// log-weight summed step by step into acc.
+template <int MODEL, bool WALL>
+__device__ __forceinline__ void steps4_pow(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t k,
+                                           const PhiloxKeys& keys, float twouv, float& phi, float& mn,
+                                           float& acc) {
+    uint32_t w[4];
+    philox_block(pl, k, keys, w);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
+        const float q = __fmul_rn(model.kq, np.rho);
+        phi = model.advance(phi, q, np.c, acc);
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        mn = fminf(mn, phi);
+        phi = model.advance(phi, q, np.s, acc);
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        mn = fminf(mn, phi);
+    }
+}
 
 // Four binary32 EM steps from one Philox block (two Box–Muller pairs): the
 // state update, the wall, the block minimum and the running sum of
@@ -133,6 +205,29 @@ struct ModelStep<double, FPT_MODEL_CONSTANT> {
     }
     __device__ __forceinline__ double step(double phi, double xi) const {
         return phi + (a0 + b * s0) * dN + s0 * xi * sq;
+    }
+};
+
+// Quadratic potential with B = A_p phi^p (§3.5 Eq. (26)), binary64: the update
+// of Eq. (11) and the step's log-weight -(B/S^2)(B dN/2 + S xi sqrt(dN)) of
+// Eqs. (12)-(14), as written.
+template <int MODEL>
+struct ModelStep<double, MODEL> {
+    static_assert(MODEL == kModelPowReal, "binary64 model tag");
+    double cm, A, p, dN, sq;
+    __device__ __forceinline__ void load(const SetConst& s) {
+        cm = s.cm;
+        A = s.b;
+        p = s.pw;
+        dN = s.dN;
+        sq = s.sq;
+    }
+    __device__ __forceinline__ double advance(double phi, double xi, double& acc) const {
+        const double D = -2.0 / phi;
+        const double S = cm * phi;
+        const double B = A * pow(phi, p);
+        acc -= (B / (S * S)) * (0.5 * B * dN + S * xi * sq);
+        return phi + (D + B) * dN + S * xi * sq;
     }
 };
 
@@ -283,9 +378,13 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
                     if (M == 0) {
                         const float trig = h == 0 ? np.c : np.s;
                         prev = ph;
-                        ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                        if constexpr (is_pow_model(MODEL)) {
+                            ph = model.advance(ph, q, trig, s2);
+                        } else {
+                            ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                            s2 = __fmaf_rn(np.rho, trig, s2);
+                        }
                         if constexpr (WALL) ph = fminf(ph, twouv - ph);
-                        s2 = __fmaf_rn(np.rho, trig, s2);
                         const int step_index = e.m0 + 4 * g + 2 * p + h;
                         if (ph <= phi_end) {
                             crossed = true;
@@ -303,9 +402,13 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
             for (int q4 = 0; q4 < 4; ++q4) {
                 if (M == 0) {
                     prev = ph;
-                    ph = model.step(ph, xi[q4]);
+                    if constexpr (is_pow_model(MODEL)) {
+                        ph = model.advance(ph, xi[q4], s2);
+                    } else {
+                        ph = model.step(ph, xi[q4]);
+                        s2 += xi[q4];
+                    }
                     if constexpr (WALL) ph = real_min<Real>(ph, twouv - ph);
-                    s2 += xi[q4];
                     const int step_index = e.m0 + 4 * g + q4;
                     if (ph <= phi_end) {
                         crossed = true;
@@ -318,8 +421,10 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
         }
         if (__all_sync(mask, M != 0)) break;
     }
-    // sum of the normals (binary32 sums are in rho units)
-    const double Wtot = sizeof(Real) == 4 ? kXiPerRho * e.W.total(s2) : (double)e.W.total(s2);
+    // constant bias: W is the sum of the normals (binary32 sums in rho units);
+    // power models: W is ln w itself
+    const double Wtot = (sizeof(Real) == 4 && !is_pow_model(MODEL)) ? kXiPerRho * e.W.total(s2)
+                                                                     : (double)e.W.total(s2);
     double N;
     if (crossed) {
         // linear interpolation of the crossing inside step M-1, in binary64
@@ -330,7 +435,7 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
         N = __longlong_as_double(0x7ff0000000000000ll);  // +inf: censored
     }
     P.out_N[e.rec] = N;
-    P.out_logw[e.rec] = -S.lw_bsq * Wtot - S.lw_half_b2dN * (double)M;
+    P.out_logw[e.rec] = is_pow_model(MODEL) ? Wtot : -S.lw_bsq * Wtot - S.lw_half_b2dN * (double)M;
     my_steps += (unsigned long long)M;
 }
 
@@ -435,17 +540,23 @@ stepper_kernel(const StepperParams P) {
         const uint32_t k0 = (uint32_t)m0 >> 2;
 #pragma unroll
         for (int g = 0; g < KS / 4; ++g) {
-            if constexpr (sizeof(Real) == 4) {
+            if constexpr (sizeof(Real) == 4 && is_pow_model(MODEL)) {
+                steps4_pow<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
+            } else if constexpr (sizeof(Real) == 4) {
                 steps4_f32<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
             } else {
                 Real xi[4];
                 normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
-                    phi = model.step(phi, xi[q4]);
+                    if constexpr (is_pow_model(MODEL)) {
+                        phi = model.advance(phi, xi[q4], sblk);
+                    } else {
+                        phi = model.step(phi, xi[q4]);
+                        sblk += xi[q4];
+                    }
                     if constexpr (WALL) phi = real_min<Real>(phi, twouv - phi);  // mirror at phi_uv
                     mn = real_min<Real>(mn, phi);
-                    sblk += xi[q4];
                 }
             }
         }

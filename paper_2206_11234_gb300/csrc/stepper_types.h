@@ -9,6 +9,13 @@ namespace fpt {
 
 constexpr int kStepperMaxThreads = 512;
 
+// Model tags of the quadratic potential with the power-law bias B = A_p phi^p
+// (§3.5 Eq. (26)): kModelPow + p for an integer p in 0..4 (phi^(p-1) by
+// multiplies), kModelPowReal for any real p (phi^(p-1) = 2^((p-1) log2 phi)).
+constexpr int kModelPow = 16;
+constexpr int kModelPowReal = kModelPow + 15;
+__host__ __device__ constexpr bool is_pow_model(int model) { return model >= kModelPow; }
+
 // Per parameter set, prepared on the host (binary64 originals and the
 // binary32 step constants), copied to shared memory by every block.
 struct SetConst {
@@ -25,6 +32,10 @@ struct SetConst {
     float f_c1, f_c2, f_c3;                 // binary32 step constants (see ModelStep)
     float f_cmdN;                           // c0 m dN: the bias part of dphi/phi is b * f_cmdN
     float f_dN, f_sq;                       // dN and sqrt(dN) in binary32 (learned-bias stepper)
+    // power-law bias B = A_p phi^p (A_p in b): the exponent, and the binary32
+    // weight constants of ModelStep for the power models (stepper.cuh)
+    double pw;
+    float f_pm1, f_pw1, f_pw2;              // p - 1, -A_p/(c m)^2, -A_p^2 dN/(2 (c m)^2)
 };
 
 // Bytes of the per-set table at the start of the stepper's dynamic shared

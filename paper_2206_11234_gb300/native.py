@@ -31,6 +31,7 @@ PREC_F32_KAHAN = 1
 PREC_F32_F64ACC = 2
 PRECISIONS = {"f64": PREC_F64, "f32_kahan": PREC_F32_KAHAN, "f32_f64acc": PREC_F32_F64ACC}
 BIAS_CONST = 0
+BIAS_POWER = 1
 BIAS_MLP = 2
 MAX_SETS = 64
 MAX_HIST_BINS = 4096
@@ -46,6 +47,7 @@ class FptParams(ctypes.Structure):
         ("a0", ctypes.c_double),
         ("s0", ctypes.c_double),
         ("n_max", ctypes.c_double),
+        ("bias_p", ctypes.c_double),
         ("mlp", ctypes.c_void_p),
         ("k_eval", ctypes.c_int32),
         ("block_dim", ctypes.c_int32),
@@ -183,12 +185,20 @@ def _stream(stream) -> Optional[int]:
 def make_params(*, model=MODEL_QUADRATIC, precision=PREC_F64, m=1.0, a0=0.0, s0=0.0, n_max,
                 block_dim=0, k_steps=0, set_id=0, traj_offset=0, stream=None,
                 steps_out: Optional[torch.Tensor] = None, mlp: Optional[torch.Tensor] = None,
-                k_eval: int = 0) -> FptParams:
+                k_eval: int = 0, bias_p: Optional[float] = None) -> FptParams:
+    """Launch parameters.  The bias is B = b S (the sets' b) by default, the
+    power law B = b phi^bias_p when bias_p is given, the learned b(phi, N) S
+    when mlp is given."""
     p = FptParams()
     p.abi_version = FPT_ABI_VERSION
     p.model = model
     p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
     p.bias_kind = BIAS_CONST if mlp is None else BIAS_MLP
+    if bias_p is not None:
+        if mlp is not None:
+            raise ValueError("bias_p and mlp exclude each other")
+        p.bias_kind = BIAS_POWER
+        p.bias_p = bias_p
     p.m, p.a0, p.s0, p.n_max = m, a0, s0, n_max
     p.mlp = None if mlp is None else mlp.data_ptr()
     p.k_eval = k_eval
