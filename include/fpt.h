@@ -229,6 +229,16 @@ typedef struct fpt_estimate_bin {
 int fpt_estimate(const fpt_bin* bins, int32_t n_bins, int32_t n_sub, double lo, double hi,
                  int64_t n_total, uint64_t id_offset, fpt_estimate_bin* out, void* stream);
 
+/* Pearson's correlation coefficient of (N_i, ln w_i) over the runs with finite
+ * N_i (§3.5: |r| of log10 w with N measures how tightly the (N, w) cloud is
+ * squeezed and guides the choice of the bias; log10 w and ln w differ by a
+ * constant factor, which r does not see).  N, logw: device double[n].  Two
+ * passes in binary64: means, then centred sums.  out: device double[8] =
+ * {r, count, mean_N, mean_lw, var_N, var_lw, cov, 0} with unbiased variances
+ * and covariance; r = NaN when fewer than 2 runs or a variance is zero; the
+ * 8 doubles are also the reduction's work area.  Asynchronous on `stream`. */
+int fpt_pearson(const double* N, const double* logw, int64_t n, double* out, void* stream);
+
 /* One training record of the learned-bias stepper: the MLP inputs at the start
  * of a k_eval-step block of run `run` (its record index in the call's outputs)
  * and the sum of the normals drawn in that block (up to the run's last step).

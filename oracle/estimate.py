@@ -160,3 +160,25 @@ def estimate(N, logw, n_bins, lo, hi, n_sub=1, id_offset=0):
             out["jk_direct"][b] = np.std(pd, ddof=1) / math.sqrt(n_sub)
             out["jk_lognormal"][b] = np.std(pl, ddof=1) / math.sqrt(n_sub)
     return out
+
+
+def pearson(N, logw):
+    """Pearson's r of (N, ln w) over the runs with finite N (§3.5), with the
+    count, means and unbiased (co)variances; r is NaN for fewer than 2 runs or
+    a zero variance."""
+    N = np.asarray(N, dtype=np.float64)
+    lw = np.asarray(logw, dtype=np.float64)
+    ok = np.isfinite(N)
+    x, y = N[ok], lw[ok]
+    n = x.size
+    out = {"r": math.nan, "count": float(n), "mean_N": math.nan, "mean_lw": math.nan, "var_N": math.nan,
+           "var_lw": math.nan, "cov": math.nan}
+    if n >= 1:
+        out["mean_N"], out["mean_lw"] = float(x.mean()), float(y.mean())
+    if n >= 2:
+        dx, dy = x - x.mean(), y - y.mean()
+        sxx, syy, sxy = float(np.sum(dx * dx)), float(np.sum(dy * dy)), float(np.sum(dx * dy))
+        out["var_N"], out["var_lw"], out["cov"] = sxx / (n - 1), syy / (n - 1), sxy / (n - 1)
+        if sxx > 0 and syy > 0:
+            out["r"] = sxy / math.sqrt(sxx * syy)
+    return out

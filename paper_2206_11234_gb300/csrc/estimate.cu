@@ -3,7 +3,8 @@
 // §2.2 Eq. (16)) with its standard error, the lognormal estimate and its error
 // bars (§2.4 Eqs. (22)-(24)), the D'Agostino-Pearson normality test of ln w
 // that decides whether the lognormal estimate applies (§2.4), and jackknife
-// errors over the histogram's n_sub subsets (§2.1).
+// errors over the histogram's n_sub subsets (§2.1); and Pearson's r of
+// (N, ln w) over all runs, the measure of §3.5's search for the power-law bias.
 //
 // One thread per bin, binary64 throughout.  The thread reads the bin's n_sub
 // subset entries, each holding max-shifted sums about its own maximum, and
@@ -20,6 +21,7 @@
 // and D'Agostino 1990).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -200,10 +202,112 @@ __global__ void estimate_kernel(const fpt_bin* __restrict__ bins, int n_bins, in
     out[j] = o;
 }
 
+// ---- Pearson's r of (N, ln w) over the finite runs ----
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // sh is reused by consecutive calls
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// pass 1: count, sum N, sum ln w -> out[1..3]
+__global__ void pearson_pass1(const double* __restrict__ N, const double* __restrict__ lw, long long n,
+                              double* __restrict__ out) {
+    __shared__ double sh[32];
+    double c = 0.0, sn = 0.0, sl = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = N[i];
+        if (isfinite(x)) {
+            c += 1.0;
+            sn += x;
+            sl += lw[i];
+        }
+    }
+    c = block_sum(c, sh);
+    sn = block_sum(sn, sh);
+    sl = block_sum(sl, sh);
+    if (threadIdx.x == 0 && c > 0.0) {
+        atomicAdd(&out[1], c);
+        atomicAdd(&out[2], sn);
+        atomicAdd(&out[3], sl);
+    }
+}
+
+// pass 2: centred sums of squares and products -> out[4..6]
+__global__ void pearson_pass2(const double* __restrict__ N, const double* __restrict__ lw, long long n,
+                              double* __restrict__ out) {
+    __shared__ double sh[32];
+    const double cnt = out[1];
+    if (cnt == 0.0) return;
+    const double mn = out[2] / cnt, ml = out[3] / cnt;
+    double sxx = 0.0, syy = 0.0, sxy = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = N[i];
+        if (isfinite(x)) {
+            const double dx = x - mn, dy = lw[i] - ml;
+            sxx += dx * dx;
+            syy += dy * dy;
+            sxy += dx * dy;
+        }
+    }
+    sxx = block_sum(sxx, sh);
+    syy = block_sum(syy, sh);
+    sxy = block_sum(sxy, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&out[4], sxx);
+        atomicAdd(&out[5], syy);
+        atomicAdd(&out[6], sxy);
+    }
+}
+
+__global__ void pearson_final(double* out) {
+    const double c = out[1], sxx = out[4], syy = out[5], sxy = out[6];
+    const double qnan = nan("");
+    out[0] = (c >= 2.0 && sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : qnan;
+    out[2] = c > 0.0 ? out[2] / c : qnan;
+    out[3] = c > 0.0 ? out[3] / c : qnan;
+    out[4] = c >= 2.0 ? sxx / (c - 1.0) : qnan;
+    out[5] = c >= 2.0 ? syy / (c - 1.0) : qnan;
+    out[6] = c >= 2.0 ? sxy / (c - 1.0) : qnan;
+    out[7] = 0.0;
+}
+
 }  // namespace
 }  // namespace fpt
 
 using namespace fpt;
+
+extern "C" int fpt_pearson(const double* N, const double* logw, int64_t n, double* out, void* stream) {
+    if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);
+    if (!out || (n > 0 && (!N || !logw))) return fail(FPT_EINVAL, "pointer is NULL");
+    int n_sm = 0;
+    int rc = device_sm_count(&n_sm);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, 8 * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "pearson reset");
+    const int threads = 256;
+    long long want = (n + threads - 1) / threads;
+    const int grid = (int)std::max(1LL, std::min(want, 2LL * n_sm));
+    if (n > 0) {
+        pearson_pass1<<<grid, threads, 0, st>>>(N, logw, (long long)n, out);
+        pearson_pass2<<<grid, threads, 0, st>>>(N, logw, (long long)n, out);
+    }
+    pearson_final<<<1, 1, 0, st>>>(out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pearson launch");
+    return FPT_OK;
+}
 
 extern "C" int fpt_estimate(const fpt_bin* bins, int32_t n_bins, int32_t n_sub, double lo, double hi,
                             int64_t n_total, uint64_t id_offset, fpt_estimate_bin* out, void* stream) {

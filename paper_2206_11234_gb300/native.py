@@ -133,6 +133,7 @@ def _load():
     L.fpt_simulate_batch_host.argtypes = [P(FptParams), P(FptSet), i32, u64, vp, vp, vp, vp]
     L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
     L.fpt_estimate.argtypes = [vp, i32, i32, d, d, i64, u64, vp, vp]
+    L.fpt_pearson.argtypes = [vp, vp, i64, vp, vp]
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -295,6 +296,20 @@ def fpt_estimate(bins: torch.Tensor, n_bins: int, lo: float, hi: float, n_total:
         raise ValueError("out must be float64 with 16 values per bin")
     _check(lib.fpt_estimate(_dptr(bins), n_bins, n_sub, lo, hi, n_total, id_offset, _dptr(out),
                             _stream(stream)))
+
+
+PEARSON_FIELDS = ("r", "count", "mean_N", "mean_lw", "var_N", "var_lw", "cov")
+
+
+def fpt_pearson(N: torch.Tensor, logw: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> dict:
+    """Pearson's r of (N, ln w) over the runs with finite N (device reduction);
+    returns {field: float} for PEARSON_FIELDS (synchronises the stream)."""
+    if out is None:
+        out = torch.empty(8, dtype=torch.float64, device=N.device)
+    _check(lib.fpt_pearson(_dptr(N, torch.float64), _dptr(logw, torch.float64), N.numel(), _dptr(out, torch.float64),
+                           _stream(stream)))
+    v = out.cpu().tolist()
+    return {f: v[i] for i, f in enumerate(PEARSON_FIELDS)}
 
 
 def fpt_normals(seed: int, traj: int, set_id: int, k0: int, n_blocks: int, precision, out: torch.Tensor,

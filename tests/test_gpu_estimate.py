@@ -124,3 +124,21 @@ def test_lognormal_rule_on_simulated_runs(nat):
     assert big.sum() >= 20
     assert np.median(got["p_normal"][big]) < 1e-10
     assert not nat.lognormal_applies(got)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 1000, 1 << 20])
+def test_pearson_matches_oracle(nat, n):
+    import torch
+    rng = np.random.default_rng(n + 3)
+    N = rng.normal(8.5, 0.02, n)
+    lw = -2.0 * (N - 8.5) / 0.02 + rng.normal(0, 0.5, n) - 40.0
+    if n > 10:
+        N[rng.random(n) < 0.01] = np.inf
+    got = nat.fpt_pearson(torch.from_numpy(N).cuda(), torch.from_numpy(lw).cuda())
+    ref = OE.pearson(N, lw)
+    assert got["count"] == ref["count"]
+    for f in ("r", "mean_N", "mean_lw", "var_N", "var_lw", "cov"):
+        if math.isnan(ref[f]):
+            assert math.isnan(got[f]), f
+        else:
+            assert math.isclose(got[f], ref[f], rel_tol=1e-10, abs_tol=1e-300), (f, got[f], ref[f])

@@ -122,3 +122,21 @@ def test_edge_cases():
     assert o["p_direct"][2] == 0 and o["p_lognormal"][2] == 0 and o["eps_hi"][2] == 0
     assert np.all(np.isnan(o["k2"]))                # fewer than 8 runs
     assert math.isnan(o["jk_lognormal"][1])         # subset 1 holds one run of bin 1
+
+
+def test_pearson_matches_scipy_and_exact_cases():
+    rng = np.random.default_rng(8)
+    N = rng.normal(8.5, 0.02, 5000)
+    lw = -3.0 * (N - 8.5) / 0.02 + rng.normal(0, 1.0, N.size)
+    N[::97] = np.inf
+    o = E.pearson(N, lw)
+    ok = np.isfinite(N)
+    assert math.isclose(o["r"], stats.pearsonr(N[ok], lw[ok]).statistic, rel_tol=1e-12)
+    assert o["count"] == ok.sum()
+    assert math.isclose(o["cov"], np.cov(N[ok], lw[ok])[0, 1], rel_tol=1e-12)
+    # exactly linear: r = +-1; constant: undefined
+    x = np.linspace(1.0, 2.0, 11)
+    assert math.isclose(E.pearson(x, 3 * x - 1)["r"], 1.0, rel_tol=1e-14)
+    assert math.isclose(E.pearson(x, -0.5 * x)["r"], -1.0, rel_tol=1e-14)
+    assert math.isnan(E.pearson(x, np.zeros(11))["r"])
+    assert math.isnan(E.pearson(np.array([np.inf, 1.0]), np.zeros(2))["r"])
