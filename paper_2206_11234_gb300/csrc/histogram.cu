@@ -9,7 +9,8 @@
 //   pass 1: classify each record, per-bin max of ln w (shared-memory atomicMax
 //           on an order-preserving 64-bit key, one global atomic per bin and block);
 //   pass 2: max-shifted sums into shared-memory bins, lanes of a warp that hit
-//           the same bin (__match_any_sync) combined before one shared atomic.
+//           the same bin (__match_any_sync) combined by their lowest lane, one
+//           peer per shuffle round, before one shared atomic per bin and warp.
 // Bins are right-closed: j = ceil((N - lo)/d) - 1, clamped to [0, n_bins).
 #include <cuda_runtime.h>
 
@@ -94,13 +95,18 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
             if (cat == 0) key = ord_key(lw[r]);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        // max over the lanes that share this lane's bin
+        // the group leader (lowest lane of the bin) takes the max over its peers,
+        // one peer per round: as many rounds as the largest group has members - 1
+        const bool leader = (int)lane == __ffs(peers) - 1;
+        unsigned rem = (leader && bin >= 0) ? (peers & ~(1u << lane)) : 0u;
         unsigned long long best = key;
-        for (int src = 0; src < 32; ++src) {
+        while (__any_sync(0xffffffffu, rem != 0u)) {
+            const int src = rem ? __ffs(rem) - 1 : (int)lane;
             const unsigned long long v = __shfl_sync(0xffffffffu, key, src);
-            if ((peers >> src) & 1u) best = v > best ? v : best;
+            if (rem) best = v > best ? v : best;
+            rem &= rem - 1u;
         }
-        if (bin >= 0 && (int)lane == __ffs(peers) - 1) atomicMax(&s_key[bin], best);
+        if (bin >= 0 && leader) atomicMax(&s_key[bin], best);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x)
@@ -151,28 +157,26 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        const bool alone = __popc(peers) == 1;
-        if (__all_sync(0xffffffffu, alone)) {
-            if (bin >= 0) {
+        // the group leader sums its peers' values, one peer per round (no
+        // rounds when every lane of the warp has a bin of its own)
+        const bool leader = (int)lane == __ffs(peers) - 1;
+        unsigned rem = (leader && bin >= 0) ? (peers & ~(1u << lane)) : 0u;
+        double acc[kSums];
 #pragma unroll
-                for (int f = 0; f < kSums; ++f) atomicAdd(&s_acc[kSums * bin + f], v[f]);
-                atomicAdd(&s_cnt[bin], 1ull);
-            }
-        } else {
-            double acc[kSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int src = 0; src < 32; ++src) {
-                const bool take = (peers >> src) & 1u;
+        for (int f = 0; f < kSums; ++f) acc[f] = v[f];
+        while (__any_sync(0xffffffffu, rem != 0u)) {
+            const int src = rem ? __ffs(rem) - 1 : (int)lane;
 #pragma unroll
-                for (int f = 0; f < kSums; ++f) {
-                    const double y = __shfl_sync(0xffffffffu, v[f], src);
-                    if (take) acc[f] += y;
-                }
+            for (int f = 0; f < kSums; ++f) {
+                const double y = __shfl_sync(0xffffffffu, v[f], src);
+                if (rem) acc[f] += y;
             }
-            if (bin >= 0 && (int)lane == __ffs(peers) - 1) {
+            rem &= rem - 1u;
+        }
+        if (bin >= 0 && leader) {
 #pragma unroll
-                for (int f = 0; f < kSums; ++f) atomicAdd(&s_acc[kSums * bin + f], acc[f]);
-                atomicAdd(&s_cnt[bin], (unsigned long long)__popc(peers));
-            }
+            for (int f = 0; f < kSums; ++f) atomicAdd(&s_acc[kSums * bin + f], acc[f]);
+            atomicAdd(&s_cnt[bin], (unsigned long long)__popc(peers));
         }
     }
     __syncthreads();
