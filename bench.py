@@ -37,6 +37,38 @@ ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 scheduler
 MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock
 
 
+# Sources the binary32 stepper kernel is built from: DRAM counters recorded
+# for it in profiles/ apply only while these files are unchanged.
+STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h")
+
+
+def stepper_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2206_11234_gb300", "csrc")
+    for f in STEPPER_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def stepper_traffic(precision, block_dim, k_steps, runs):
+    """DRAM bytes (read + write) of one stepper launch over `runs` runs, scaled
+    from the ncu capture recorded in profiles/stepper_dram_traffic.json; None
+    when no capture matches this kernel, launch shape and source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "stepper_dram_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if (rec.get("precision"), rec.get("block_dim"), rec.get("k_steps")) != (precision, block_dim, k_steps):
+        return None
+    if rec.get("source_sha256") != stepper_source_hash():
+        return None
+    return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * runs / rec["runs"]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,7 +623,7 @@ def main():
             es = tt[1].item()
         import ctypes
         h2d = ctypes.sizeof(nat.FptSet) * len(specs) + ctypes.sizeof(nat.FptParams)
-        d2h = 2 * 8 * n + 48 * nbins + 32 * len(specs)
+        d2h = 2 * 8 * n + ctypes.sizeof(nat.FptBin) * nbins + ctypes.sizeof(nat.FptHistCounts) * len(specs)
         e2e = {"value": es / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
@@ -606,9 +638,11 @@ def main():
     issue_peak = n_sm * ISSUE_PER_SM_CLK * f_max  # warp-instructions/s
     steps_peak = min(issue_peak / ALG_INST_PER_STEP, n_sm * MUFU_PER_SM_CLK * f_max / MUFU_PER_STEP) * 32
     achieved_steps = stepper_steps / (ms_stepper / 1e3)
+    shape = tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}
     roof = {"bound": "alu", "achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9,
             "peak": issue_peak / 1e9, "unit": "Gwarp-inst/s (algorithmic)",
-            "frac": achieved_steps / steps_peak, "traffic": None,
+            "frac": achieved_steps / steps_peak,
+            "traffic": stepper_traffic(wl.precision, shape.get("block_dim"), shape.get("k_steps"), n),
             "kernel": f"stepper_kernel<float, {wl.precision}, quadratic, "
                       f"k_steps {(tuned or {}).get('k_steps', args.k_steps)}>",
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
