@@ -39,7 +39,7 @@ MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock
 
 # Sources the binary32 stepper kernel is built from: DRAM counters recorded
 # for it in profiles/ apply only while these files are unchanged.
-STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h")
+STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h", "../build.py")
 
 
 def stepper_source_hash() -> str:

@@ -442,11 +442,14 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-// Register cap per thread.  48 keeps the binary32 hot loop spill-free at 40
-// resident warps per SM (5 blocks of 256); the binary64 reference kernels are
-// built with a larger cap.
+// Register cap per thread.  56 leaves every binary32 instantiation spill-free
+// (48 spilled a few words in the Kahan and power-law variants) at 32 resident
+// warps per SM; measured on the drift-dominated ladder, 40 / 48 / 56 gave
+// 1.113 / 1.116 / 1.131 e12 steps/s whatever the block size, so occupancy is
+// not what bounds the loop.  The binary64 reference kernels are built with a
+// larger cap.
 #ifndef FPT_STEPPER_MAXNREG
-#define FPT_STEPPER_MAXNREG 48
+#define FPT_STEPPER_MAXNREG 56
 #endif
 template <typename Real, int PREC, int MODEL, bool WALL, int KS>
 __global__ void __maxnreg__(FPT_STEPPER_MAXNREG)
