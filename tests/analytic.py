@@ -17,6 +17,18 @@ Monte Carlo must reproduce.
 * ``inverse_gaussian``: first-passage law of Brownian motion with constant
   drift (the constant test model), via scipy.stats.invgauss, with the
   Broadie–Glasserman–Kou continuity correction for discrete monitoring.
+* ``backward_raw_moments``: <N^k>, k = 1..K, from the chain of backward
+  equations L T_k = -k T_{k-1} (T_0 = 1) — the moments that Appendix B
+  Eq. (B.12) takes from derivatives of the characteristic function at t = 0.
+* ``generator_eigenvalues``: the smallest decay rates of the same finite
+  difference generator (the poles Lambda_n of Appendix A, Eq. (A.7)).
+* ``quad_poles``, ``quad_pole_residues``, ``quad_tail_from_poles``: Appendix A
+  for quadratic inflation with a reflecting wall — the pole equation A = B
+  (Eq. (A.16)) solved on the negative imaginary t axis, the residues by
+  l'Hopital's rule (Eq. (A.18)), and P(N), Q(N) as sums of decaying
+  exponentials (Eqs. (A.7), (A.19)); confluent hypergeometric functions from mpmath.
+* ``edgeworth_pdf``: Appendix B, Eq. (B.10), with the probabilists' Hermite
+  polynomial He_3(x) = x^3 - 3x (Eq. (B.7) prints x^2 - 1).
 """
 import math
 import warnings
@@ -110,6 +122,181 @@ def backward_moments_fd(phi_in, drift, noise, phi_end, phi_uv, n=20001):
     m1 = float(np.interp(phi_in, x, T1))
     m2 = float(np.interp(phi_in, x, T2))
     return m1, m2 - m1 * m1
+
+
+def backward_raw_moments(phi_in, drift, noise, phi_end, phi_uv, k_max=4, n=20001):
+    """[<N>, <N^2>, ..., <N^k_max>] at phi_in: L T_k = -k T_{k-1}, T_0 = 1,
+    T_k(phi_end) = 0, T_k'(phi_uv) = 0 (second-order finite differences)."""
+    x = np.linspace(phi_end, phi_uv, n)
+    solve = spla.factorized(_grid_operator(x, drift, noise).tocsc())
+    T = np.ones(n)
+    out = []
+    for k in range(1, k_max + 1):
+        r = -k * T
+        r[0] = 0.0
+        T = solve(r)
+        out.append(float(np.interp(phi_in, x, T)))
+    return out
+
+
+def backward_cumulants(phi_in, drift, noise, phi_end, phi_uv, n=20001):
+    """(kappa_1..kappa_4) of N at phi_in.  With chi = exp(K), K = sum kappa_n
+    (it)^n / n!, the equation L chi = -it chi (L = a d2 + D d, a = S^2/2: the
+    generator of Eq. (A.2)) gives, order by order in it,
+        L k1 = -1,  L k2 = -2 a k1'^2,  L k3 = -6 a k1' k2',
+        L k4 = -a (6 k2'^2 + 8 k1' k3'),
+    with k_n(phi_end) = 0, k_n'(phi_uv) = 0: the cumulants without the
+    cancellation of raw moments (Appendix B needs them at a few sigma / <N>)."""
+    x = np.linspace(phi_end, phi_uv, n)
+    a = noise(x) ** 2 / 2.0
+    solve = spla.factorized(_grid_operator(x, drift, noise).tocsc())
+
+    def sol(rhs):
+        r = np.array(rhs, dtype=np.float64)
+        r[0] = 0.0
+        return solve(r)
+    d = lambda f: np.gradient(f, x)
+    k1 = sol(-np.ones(n))
+    d1 = d(k1)
+    k2 = sol(-2 * a * d1 ** 2)
+    d2 = d(k2)
+    k3 = sol(-6 * a * d1 * d2)
+    d3 = d(k3)
+    k4 = sol(-a * (6 * d2 ** 2 + 8 * d1 * d3))
+    return tuple(float(np.interp(phi_in, x, k)) for k in (k1, k2, k3, k4))
+
+
+def generator_eigenvalues(drift, noise, phi_end, phi_uv, k=3, n=20001):
+    """The k smallest decay rates Lambda of L psi = -Lambda psi, psi(phi_end) = 0,
+    psi'(phi_uv) = 0 (finite differences, shift-invert about 0)."""
+    x = np.linspace(phi_end, phi_uv, n)
+    L = _grid_operator(x, drift, noise).tolil()
+    L = L[1:, 1:].tocsc()  # eliminate the Dirichlet node
+    vals = spla.eigs(L, k=k, sigma=0.0, which="LM", return_eigenvectors=False)
+    return np.sort(-vals.real)
+
+
+# ---- Appendix A: poles and residues for quadratic inflation with a wall ----
+
+def _mp():
+    import mpmath  # test-only dependency, available where the CPU tests run
+    return mpmath
+
+
+def _quad_f(mp, m, alpha, phi):
+    """f(t, phi) of Eq. (A.11) and df/dphi, with v = m^2 phi^2 / (48 pi^2)
+    (the reduced potential V / (24 pi^2) of Eq. (A.3) for V = m^2 phi^2 / 2);
+    g is the same with alpha -> -alpha."""
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+    v = v0 * mp.mpf(phi) ** 2
+    a, b = (-1 - alpha) / 4, 1 - alpha / 2
+    z = -1 / v
+    M = mp.hyp1f1(a, b, z)
+    dM = a / b * mp.hyp1f1(a + 1, b + 1, z)  # d/dz 1F1(a; b; z)
+    e = (1 + alpha) / 4
+    f = v ** e * M
+    dfdv = e * v ** (e - 1) * M + v ** e * dM / v ** 2
+    return f, dfdv * 2 * v0 * mp.mpf(phi)
+
+
+def _pole_function(mp, m, phi_end, phi_uv, kappa):
+    """On t = -i Lambda with Lambda > v0/4, alpha = i kappa and g = conj(f), so
+    A = B (Eq. (A.16)) is the real condition Im[f'(phi_uv) conj(f(phi_end))] = 0."""
+    al = 1j * mp.mpf(kappa)
+    fe, _ = _quad_f(mp, m, al, phi_end)
+    _, fu = _quad_f(mp, m, al, phi_uv)
+    return mp.im(fu * mp.conj(fe))
+
+
+def quad_poles(m, phi_uv, n_poles, phi_end=math.sqrt(2.0), dps=40, dk=0.5):
+    """[(Lambda_n, kappa_n)] for n < n_poles: roots kappa > 0 of the pole
+    equation (kappa = 0, where f = g and A = B trivially, is no pole), bracketed
+    on a grid of step dk and refined; Lambda = v0 (1 + kappa^2) / 4."""
+    mp = _mp()
+    mp.mp.dps = dps
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+    F = lambda k: _pole_function(mp, m, phi_end, phi_uv, k)
+    out = []
+    k0, f0 = dk, F(dk)
+    while len(out) < n_poles:
+        k1 = k0 + dk
+        f1 = F(k1)
+        if f0 * f1 < 0:
+            r = mp.findroot(F, (k0, k1), solver="anderson")
+            out.append((float(v0 * (1 + r * r) / 4), r))
+        k0, f0 = k1, f1
+    return out
+
+
+def quad_pole_residues(m, phi_uv, phi, poles, phi_end=math.sqrt(2.0), dps=40):
+    """a_n(phi) of Eq. (A.18): -i N(t_n) / D'(t_n) with N = B f/f_end - A g/g_end,
+    D = B - A, A = f'_uv / g'_uv, B = f_end / g_end (Eq. (A.14)).  D' is taken
+    along kappa (t = -i v0 (1 + kappa^2)/4, dt/dkappa = -i v0 kappa / 2), which
+    keeps the derivative off the branch cut of alpha(t)."""
+    mp = _mp()
+    mp.mp.dps = dps
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+
+    def AB(k):
+        al = 1j * k
+        fe, _ = _quad_f(mp, m, al, phi_end)
+        ge, _ = _quad_f(mp, m, -al, phi_end)
+        _, fu = _quad_f(mp, m, al, phi_uv)
+        _, gu = _quad_f(mp, m, -al, phi_uv)
+        return fu / gu, fe / ge, fe, ge
+
+    res = []
+    for _, k in poles:
+        A, B, fe, ge = AB(k)
+        f, _ = _quad_f(mp, m, 1j * k, phi)
+        g, _ = _quad_f(mp, m, -1j * k, phi)
+        num = B * f / fe - A * g / ge
+        dD = mp.diff(lambda kk: AB(kk)[1] - AB(kk)[0], k) / (-1j * v0 * k / 2)
+        a = -1j * num / dD
+        res.append(float(mp.re(a)))
+    return res
+
+
+def quad_tail_from_poles(m, phi_uv, phi_in, N_values, n_poles=12, phi_end=math.sqrt(2.0)):
+    """(P(N), Q(N) = P(N' > N)) at phi_in from the first n_poles terms of Eq. (A.7)."""
+    poles = quad_poles(m, phi_uv, n_poles, phi_end)
+    a = quad_pole_residues(m, phi_uv, phi_in, poles, phi_end)
+    lam = np.array([p[0] for p in poles])
+    a = np.array(a)
+    N = np.asarray(N_values, dtype=np.float64)[:, None]
+    P = np.sum(a * np.exp(-lam * N), axis=1)
+    Q = np.sum(a / lam * np.exp(-lam * N), axis=1)
+    return P, Q, lam, a
+
+
+# ---- Appendix B: Edgeworth expansion ----
+
+def hermite_he(k, x):
+    """Probabilists' Hermite polynomials He_3, He_4, He_6."""
+    if k == 3:
+        return x ** 3 - 3 * x
+    if k == 4:
+        return x ** 4 - 6 * x ** 2 + 3
+    if k == 6:
+        return x ** 6 - 15 * x ** 4 + 45 * x ** 2 - 15
+    raise ValueError(k)
+
+
+def edgeworth_pdf(x, mu, sigma, gamma, kappa):
+    """Eq. (B.10): Gaussian times 1 + gamma/6 He_3 + kappa/24 He_4 + gamma^2/72 He_6."""
+    z = (np.asarray(x, dtype=np.float64) - mu) / sigma
+    g = np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi * sigma * sigma)
+    return g * (1 + gamma / 6 * hermite_he(3, z) + kappa / 24 * hermite_he(4, z) + gamma ** 2 / 72 * hermite_he(6, z))
+
+
+def cumulant_shape(raw):
+    """(mu, sigma, gamma, kappa) from raw moments [<N>, <N^2>, <N^3>, <N^4>]."""
+    m1, m2, m3, m4 = raw
+    var = m2 - m1 ** 2
+    c3 = m3 - 3 * m1 * m2 + 2 * m1 ** 3
+    c4 = m4 - 4 * m1 * m3 + 6 * m1 ** 2 * m2 - 3 * m1 ** 4
+    s = math.sqrt(var)
+    return m1, s, c3 / s ** 3, c4 / var ** 2 - 3
 
 
 def survival_pde(phi_in, drift, noise, phi_end, phi_uv, N_grid, n=4001, dN=2e-3):
