@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="drift_ladder",
                     choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall",
-                             "learned_bias", "estimators", "power_bias"])
+                             "learned_bias", "estimators", "power_bias", "multi_bias"])
     ap.add_argument("--train-steps", type=int, default=256, help="learned_bias: Adam steps")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned_bias: Adam learning rate")
     ap.add_argument("--k-eval", type=int, default=64, choices=(16, 32, 64, 128),
@@ -432,6 +432,78 @@ def run_power_bias(args):
                       "best_p_by_abs_r": best["p"], "rows": rows}))
 
 
+def run_multi_bias(args):
+    """The multi-bias reconstruction of §3.2 (the paper's m = 0.1 experiment):
+    quadratic inflation m = 0.1, phi_in = sqrt(42), no wall (censored at N = 20),
+    dN = 1e-3, B = A S with A in {0, 0.5, ..., 3}, 2^20 runs per amplitude
+    (binary32 state, binary64 log-weight); common bins on (9, 14] (width 0.025),
+    20 jackknife subsets; per-bin lognormal estimates (bins with >= 400 runs and
+    a normality p-value >= 0.5 %) stitched in log space (fpt_stitch).  Reports
+    how deep the reconstruction reaches and whether overlapping amplitudes
+    agree within their errors."""
+    import numpy as np
+    import torch
+    from paper_2206_11234_gb300 import native as nat
+    from paper_2206_11234_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = max(1 << 14, int((1 << 20) * args.scale))
+    amps = (0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0)
+    nb, lo, hi, n_sub = 200, 9.0, 14.0, 20
+    specs = [W.SetSpec(phi_in=math.sqrt(42.0), m=0.1, b=a, dN=1e-3, n_max=20.0, n_traj=n, set_id=i, hist_lo=lo,
+                       hist_hi=hi, n_bins=nb) for i, a in enumerate(amps)]
+    wl = W.Workload("multi-bias", specs, "f32_f64acc", seed=3)
+    steps = torch.zeros(1, dtype=torch.int64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    nat.simulate_workload(W.Workload("warm", [W.SetSpec(**{**specs[0].__dict__, "n_traj": 4096})], "f32_f64acc"),
+                          with_hist=False)
+    torch.cuda.synchronize()
+    ev[0].record()
+    N, lw, _, _ = nat.simulate_workload(wl, with_hist=False, steps_out=steps)
+    ev[1].record()
+    torch.cuda.synchronize()
+    sim_s = ev[0].elapsed_time(ev[1]) / 1e3
+    est = torch.empty((len(amps), nb, len(nat.ESTIMATE_FIELDS)), dtype=torch.float64, device=dev)
+    per = []
+    for k, a in enumerate(amps):
+        Nk, lk = N[k * n:(k + 1) * n].contiguous(), lw[k * n:(k + 1) * n].contiguous()
+        bins = nat.empty_bins(nb * n_sub)
+        counts = nat.empty_counts(1)
+        nat.fpt_histogram(Nk, lk, nb, lo, hi, bins, counts, n_sub=n_sub, id_offset=k * n)
+        nat.fpt_estimate(bins, nb, lo, hi, n, est[k], n_sub=n_sub, id_offset=k * n)
+        fin = torch.isfinite(Nk)
+        per.append({"A": a, "mean_N": Nk[fin].mean().item(), "censored": int((~fin).sum().item())})
+    st = nat.fpt_stitch(est, estimator=nat.ESTIMATOR_LOGNORMAL, min_count=400, p_threshold=0.005).cpu().numpy()
+    e = est.cpu().numpy()
+    mid = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
+    ok = np.isfinite(st[:, 0])
+    # overlaps: every pair of contributing amplitudes in a bin within 4 combined errors
+    pairs = agree = 0
+    for j in np.nonzero(st[:, 4] >= 2)[0]:
+        use = []
+        for k in range(len(amps)):
+            c, pn, v = e[k, j, 0], e[k, j, 13], e[k, j, 7]
+            if c >= 400 and (pn >= 0.005 or v == 0) and e[k, j, 3] > 0:
+                use.append((math.log(e[k, j, 3]), math.sqrt(v / c + v * v / (2 * c - 2) + 1 / c)))
+        for x in range(len(use)):
+            for y in range(x + 1, len(use)):
+                pairs += 1
+                agree += abs(use[x][0] - use[y][0]) <= 4 * math.hypot(use[x][1], use[y][1])
+    for k, r in enumerate(per):
+        use = (e[k, :, 0] >= 400) & ((e[k, :, 13] >= 0.005) | (e[k, :, 7] == 0)) & (e[k, :, 3] > 0)
+        r["bins_used"] = int(use.sum())
+        r["N_range"] = [float(mid[use].min()), float(mid[use].max())] if use.any() else None
+        r["min_P"] = float(e[k, use, 3].min()) if use.any() else None
+    line = {"workload": "multi_bias", "m": 0.1, "phi_in": math.sqrt(42.0), "dN": 1e-3, "runs_per_amplitude": n,
+            "total_runs": n * len(amps), "steps": int(steps.item()), "simulate_seconds": sim_s,
+            "steps_per_s": int(steps.item()) / sim_s, "per_amplitude": per,
+            "stitched": {"bins": int(ok.sum()), "N_max": float(mid[ok].max()), "min_P": float(st[ok, 0].min()),
+                         "max_rel_err": float(st[ok, 3].max()), "median_rel_err": float(np.median(st[ok, 3]))},
+            "overlap_pairs": pairs, "overlap_agree_4sigma": agree / pairs if pairs else None,
+            "curve": [[float(x), float(p), float(a)] for x, p, a in zip(mid[ok][::10], st[ok, 0][::10], st[ok, 3][::10])]}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -470,6 +542,8 @@ def main():
         return run_estimators(args)
     if args.workload == "power_bias":
         return run_power_bias(args)
+    if args.workload == "multi_bias":
+        return run_multi_bias(args)
 
     import torch
     import torch.distributed as dist

@@ -229,6 +229,30 @@ typedef struct fpt_estimate_bin {
 int fpt_estimate(const fpt_bin* bins, int32_t n_bins, int32_t n_sub, double lo, double hi,
                  int64_t n_total, uint64_t id_offset, fpt_estimate_bin* out, void* stream);
 
+/* Multi-bias reconstruction (§3.2: simulations with different bias amplitudes
+ * probe different ranges of N and are combined where they overlap).  est:
+ * device fpt_estimate_bin[n_runs][n_bins], the estimates of the SAME bins from
+ * n_runs independent simulations (fpt_estimate).  For each bin, a run
+ * contributes if its bin holds >= min_count runs, its estimate (estimator:
+ * FPT_ESTIMATOR_DIRECT or FPT_ESTIMATOR_LOGNORMAL) is defined and > 0, and,
+ * for the lognormal estimator, p_normal >= p_threshold or var_lw = 0 (w = 1
+ * in the bin: a degenerate normal; p_threshold = 0 disables the test; §2.4
+ * uses 0.005).  Contributions are combined in log space with inverse-
+ * variance weights, ln p = sum_k ln p_k / a_k^2 / sum_k 1/a_k^2 with a_k the
+ * relative error of run k (lognormal: sqrt(a^2 + 1/n_j), Eq. (24)'s a with the
+ * relative fluctuation of the bin count added; direct: se/p), and
+ * a = 1/sqrt(sum_k 1/a_k^2).  out[j] (device): {p, eps_lo = p (1 - e^-a),
+ * eps_hi = p (e^a - 1), a, n_used, best = index of the run with the smallest
+ * a_k}; bins without a contribution: p = NaN, n_used = 0, best = -1.
+ * Asynchronous on `stream`; argument errors are synchronous. */
+#define FPT_ESTIMATOR_DIRECT 0
+#define FPT_ESTIMATOR_LOGNORMAL 1
+typedef struct fpt_stitch_bin {
+    double p, eps_lo, eps_hi, log_err, n_used, best;
+} fpt_stitch_bin;
+int fpt_stitch(const fpt_estimate_bin* est, int32_t n_runs, int32_t n_bins, int32_t estimator, int64_t min_count,
+               double p_threshold, fpt_stitch_bin* out, void* stream);
+
 /* Pearson's correlation coefficient of (N_i, ln w_i) over the runs with finite
  * N_i (§3.5: |r| of log10 w with N measures how tightly the (N, w) cloud is
  * squeezed and guides the choice of the bias; log10 w and ln w differ by a

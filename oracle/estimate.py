@@ -182,3 +182,47 @@ def pearson(N, logw):
         if sxx > 0 and syy > 0:
             out["r"] = sxy / math.sqrt(sxx * syy)
     return out
+
+
+def stitch(estimates, estimator="lognormal", min_count=400, p_threshold=0.005):
+    """Multi-bias reconstruction (§3.2): estimates = [estimate(...) of each
+    simulation over the same bins].  Per bin, a simulation contributes if its
+    bin holds >= min_count runs, its estimate is defined and > 0 and (lognormal)
+    its normality p-value >= p_threshold (0: no test); the contributions are
+    combined in log space with inverse-variance weights 1/a_k^2, a_k the
+    relative error (lognormal: sqrt(s^2/n + s^4/(2n - 2) + 1/n), Eq. (24)'s
+    spread of ln w plus the relative fluctuation of the count, which Eq. (24)
+    leaves out and which is all that remains when w = 1; direct: se/p).  Returns {p, eps_lo, eps_hi, log_err, n_used, best} arrays."""
+    n_bins = len(estimates[0]["count"])
+    out = {f: np.full(n_bins, math.nan) for f in ("p", "eps_lo", "eps_hi", "log_err", "n_used", "best")}
+    for j in range(n_bins):
+        w, lp, aa, ks = [], [], [], []
+        for k, e in enumerate(estimates):
+            n = e["count"][j]
+            if not n >= min_count:
+                continue
+            if estimator == "lognormal":
+                if p_threshold > 0 and not e["p_normal"][j] >= p_threshold and not e["var_lw"][j] == 0:
+                    continue  # zero variance (w = 1): a degenerate normal, kept
+                p = e["p_lognormal"][j]
+                s2 = e["var_lw"][j]
+                a = math.sqrt(s2 / n + s2 * s2 / (2 * n - 2) + 1.0 / n)
+            else:
+                p = e["p_direct"][j]
+                a = e["se_direct"][j] / p if p > 0 else math.nan
+            if not (p > 0 and a > 0 and math.isfinite(p) and math.isfinite(a)):
+                continue
+            w.append(1.0 / (a * a))
+            lp.append(math.log(p))
+            aa.append(a)
+            ks.append(k)
+        out["n_used"][j] = len(w)
+        out["best"][j] = -1
+        if w:
+            W = sum(w)
+            a = 1.0 / math.sqrt(W)
+            p = math.exp(sum(wi * li for wi, li in zip(w, lp)) / W)
+            out["p"][j], out["log_err"][j] = p, a
+            out["eps_lo"][j], out["eps_hi"][j] = p * (1 - math.exp(-a)), p * (math.exp(a) - 1)
+            out["best"][j] = ks[int(np.argmin(aa))]
+    return out

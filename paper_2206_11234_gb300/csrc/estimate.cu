@@ -3,8 +3,10 @@
 // §2.2 Eq. (16)) with its standard error, the lognormal estimate and its error
 // bars (§2.4 Eqs. (22)-(24)), the D'Agostino-Pearson normality test of ln w
 // that decides whether the lognormal estimate applies (§2.4), and jackknife
-// errors over the histogram's n_sub subsets (§2.1); and Pearson's r of
-// (N, ln w) over all runs, the measure of §3.5's search for the power-law bias.
+// errors over the histogram's n_sub subsets (§2.1); the multi-bias
+// reconstruction of §3.2 (estimates of the same bins from several bias
+// amplitudes, combined where they overlap); and Pearson's r of (N, ln w) over
+// all runs, the measure of §3.5's search for the power-law bias.
 //
 // One thread per bin, binary64 throughout.  The thread reads the bin's n_sub
 // subset entries, each holding max-shifted sums about its own maximum, and
@@ -202,6 +204,53 @@ __global__ void estimate_kernel(const fpt_bin* __restrict__ bins, int n_bins, in
     out[j] = o;
 }
 
+// ---- multi-bias reconstruction: inverse-variance combination in log space ----
+
+__global__ void stitch_kernel(const fpt_estimate_bin* __restrict__ est, int n_runs, int n_bins, int estimator,
+                              long long min_count, double p_threshold, fpt_stitch_bin* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_bins) return;
+    double sw = 0.0, swl = 0.0, best_a = INFINITY;
+    int used = 0, best = -1;
+    for (int k = 0; k < n_runs; ++k) {
+        const fpt_estimate_bin& e = est[(long long)k * n_bins + j];
+        if (!(e.count >= (double)min_count)) continue;
+        double p, a;
+        if (estimator == FPT_ESTIMATOR_LOGNORMAL) {
+            // w = 1 throughout the bin (var_lw = 0): a degenerate normal, the test is undefined, not failed
+            if (p_threshold > 0.0 && !(e.p_normal >= p_threshold) && !(e.var_lw == 0.0)) continue;
+            p = e.p_lognormal;
+            // Eq. (24)'s spread of ln w plus the count's own relative fluctuation 1/n_j
+            a = sqrt(e.var_lw / e.count + e.var_lw * e.var_lw / (2.0 * e.count - 2.0) + 1.0 / e.count);
+        } else {
+            p = e.p_direct;
+            a = e.se_direct / e.p_direct;
+        }
+        if (!(p > 0.0) || !(a > 0.0) || !isfinite(p) || !isfinite(a)) continue;
+        const double w = 1.0 / (a * a);
+        sw += w;
+        swl += w * log(p);
+        ++used;
+        if (a < best_a) {
+            best_a = a;
+            best = k;
+        }
+    }
+    fpt_stitch_bin o;
+    if (used > 0) {
+        const double a = 1.0 / sqrt(sw);
+        o.p = exp(swl / sw);
+        o.log_err = a;
+        o.eps_lo = -o.p * expm1(-a);
+        o.eps_hi = o.p * expm1(a);
+    } else {
+        o.p = o.eps_lo = o.eps_hi = o.log_err = nan("");
+    }
+    o.n_used = (double)used;
+    o.best = (double)best;
+    out[j] = o;
+}
+
 // ---- Pearson's r of (N, ln w) over the finite runs ----
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -286,6 +335,23 @@ __global__ void pearson_final(double* out) {
 }  // namespace fpt
 
 using namespace fpt;
+
+extern "C" int fpt_stitch(const fpt_estimate_bin* est, int32_t n_runs, int32_t n_bins, int32_t estimator,
+                          int64_t min_count, double p_threshold, fpt_stitch_bin* out, void* stream) {
+    if (!est || !out) return fail(FPT_EINVAL, "pointer is NULL");
+    if (n_runs < 1 || n_bins < 1) return fail(FPT_EINVAL, "n_runs %d and n_bins %d must be >= 1", n_runs, n_bins);
+    if (estimator != FPT_ESTIMATOR_DIRECT && estimator != FPT_ESTIMATOR_LOGNORMAL)
+        return fail(FPT_EINVAL, "unknown estimator %d", estimator);
+    if (min_count < 2) return fail(FPT_EINVAL, "min_count %lld < 2", (long long)min_count);
+    if (!(p_threshold >= 0.0 && p_threshold < 1.0)) return fail(FPT_EINVAL, "p_threshold must be in [0, 1)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int threads = 128;
+    stitch_kernel<<<(n_bins + threads - 1) / threads, threads, 0, st>>>(est, n_runs, n_bins, estimator,
+                                                                        (long long)min_count, p_threshold, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "stitch launch");
+    return FPT_OK;
+}
 
 extern "C" int fpt_pearson(const double* N, const double* logw, int64_t n, double* out, void* stream) {
     if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);

@@ -134,6 +134,7 @@ def _load():
     L.fpt_histogram.argtypes = [vp, vp, i64, i32, d, d, i32, u64, vp, vp, vp]
     L.fpt_estimate.argtypes = [vp, i32, i32, d, d, i64, u64, vp, vp]
     L.fpt_pearson.argtypes = [vp, vp, i64, vp, vp]
+    L.fpt_stitch.argtypes = [vp, i32, i32, i32, i64, d, vp, vp]
     L.fpt_normals.argtypes = [u64, u64, u32, u32, i64, i32, vp, vp]
     L.fpt_autotune.argtypes = [P(FptParams), P(FptSet), i32, u64, d, P(i32), P(i32), P(d)]
     L.fpt_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -296,6 +297,30 @@ def fpt_estimate(bins: torch.Tensor, n_bins: int, lo: float, hi: float, n_total:
         raise ValueError("out must be float64 with 16 values per bin")
     _check(lib.fpt_estimate(_dptr(bins), n_bins, n_sub, lo, hi, n_total, id_offset, _dptr(out),
                             _stream(stream)))
+
+
+ESTIMATOR_DIRECT = 0
+ESTIMATOR_LOGNORMAL = 1
+STITCH_FIELDS = ("p", "eps_lo", "eps_hi", "log_err", "n_used", "best")
+
+
+class FptStitchBin(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in STITCH_FIELDS]
+
+
+def fpt_stitch(estimates: torch.Tensor, out: Optional[torch.Tensor] = None, *, estimator=ESTIMATOR_LOGNORMAL,
+               min_count: int = 400, p_threshold: float = 0.005, stream=None) -> torch.Tensor:
+    """Multi-bias reconstruction: estimates float64[n_runs, n_bins, 16] (the
+    fpt_estimate outputs of several simulations over the same bins) ->
+    float64[n_bins, 6] (STITCH_FIELDS)."""
+    if estimates.dim() != 3 or estimates.shape[2] != len(ESTIMATE_FIELDS) or estimates.dtype != torch.float64:
+        raise ValueError("estimates must be float64[n_runs, n_bins, 16]")
+    n_runs, n_bins = estimates.shape[0], estimates.shape[1]
+    if out is None:
+        out = torch.empty((n_bins, len(STITCH_FIELDS)), dtype=torch.float64, device=estimates.device)
+    _check(lib.fpt_stitch(_dptr(estimates.contiguous()), n_runs, n_bins, estimator, min_count, p_threshold,
+                          _dptr(out), _stream(stream)))
+    return out
 
 
 PEARSON_FIELDS = ("r", "count", "mean_N", "mean_lw", "var_N", "var_lw", "cov")

@@ -38,7 +38,8 @@ def test_struct_layouts_match_header(native, tmp_path):
     the header's structs."""
     structs = {"fpt_params": native.FptParams, "fpt_set": native.FptSet, "fpt_bin": native.FptBin,
                "fpt_hist_counts": native.FptHistCounts, "fpt_mlp_train_state": native.FptMlpTrainState,
-               "fpt_mlp_train_stats": native.FptMlpTrainStats, "fpt_estimate_bin": native.FptEstimateBin}
+               "fpt_mlp_train_stats": native.FptMlpTrainStats, "fpt_estimate_bin": native.FptEstimateBin,
+               "fpt_stitch_bin": native.FptStitchBin}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fpt.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -129,6 +130,14 @@ def test_host_side_argument_checks(native):
     assert est(8, 1, 0.0, math.nan, 10) == E
     assert est(8, 1, 0.0, 1.0, 0) == E
     assert L.fpt_estimate(None, 8, 1, 0.0, 1.0, 10, 0, buf, None) == E
+    st = lambda nr, nb, est_kind, mc, pt: L.fpt_stitch(buf, nr, nb, est_kind, mc, pt, buf, None)
+    assert st(0, 8, 1, 400, 0.005) == E
+    assert st(2, 0, 1, 400, 0.005) == E
+    assert st(2, 8, 7, 400, 0.005) == E
+    assert st(2, 8, 1, 1, 0.005) == E
+    assert st(2, 8, 1, 400, 1.0) == E
+    assert st(2, 8, 1, 400, math.nan) == E
+    assert L.fpt_stitch(None, 2, 8, 1, 400, 0.0, buf, None) == E
     # batch
     sets = (native.FptSet * 2)()
     for s in sets:

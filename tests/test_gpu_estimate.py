@@ -142,3 +142,30 @@ def test_pearson_matches_oracle(nat, n):
             assert math.isnan(got[f]), f
         else:
             assert math.isclose(got[f], ref[f], rel_tol=1e-10, abs_tol=1e-300), (f, got[f], ref[f])
+
+
+def test_stitch_matches_oracle(nat):
+    """Several record sets over the same bins (shifted, with their own weight
+    spreads) through fpt_histogram -> fpt_estimate -> fpt_stitch against the
+    oracle's estimate -> stitch on the same records."""
+    import torch
+    sets = []
+    for k, (shift, spread) in enumerate(((0.0, 0.6), (0.8, 0.8), (1.6, 1.1))):
+        rng = np.random.default_rng(40 + k)
+        n = 200000
+        N = rng.normal(8.5 + shift, 0.6, n)
+        lw = -3.0 * shift - 2.0 * (N - 8.5 - shift) + spread * rng.standard_normal(n)
+        sets.append((N, lw))
+    nb, lo, hi = 60, 7.0, 12.0
+    est = torch.stack([torch.from_numpy(np.stack([_gpu_estimate(nat, N, lw, nb, lo, hi)[f] for f in nat.ESTIMATE_FIELDS],
+                                                 axis=1)) for N, lw in sets]).cuda()
+    refs = [OE.estimate(N, lw, nb, lo, hi) for N, lw in sets]
+    for kind, name in ((nat.ESTIMATOR_LOGNORMAL, "lognormal"), (nat.ESTIMATOR_DIRECT, "direct")):
+        for pt in (0.0, 0.005):
+            out = nat.fpt_stitch(est, estimator=kind, min_count=400, p_threshold=pt).cpu().numpy()
+            ref = OE.stitch(refs, estimator=name, min_count=400, p_threshold=pt)
+            np.testing.assert_array_equal(out[:, 4], ref["n_used"])
+            np.testing.assert_array_equal(out[:, 5], ref["best"])
+            for i, f in enumerate(("p", "eps_lo", "eps_hi", "log_err")):
+                np.testing.assert_allclose(out[:, i], ref[f], rtol=1e-8, equal_nan=True, err_msg=f)
+            assert (out[:, 4] >= 2).sum() >= 10  # the sets overlap

@@ -140,3 +140,62 @@ def test_pearson_matches_scipy_and_exact_cases():
     assert math.isclose(E.pearson(x, -0.5 * x)["r"], -1.0, rel_tol=1e-14)
     assert math.isnan(E.pearson(x, np.zeros(11))["r"])
     assert math.isnan(E.pearson(np.array([np.inf, 1.0]), np.zeros(2))["r"])
+
+
+def _fake_estimate(p, var, count, p_normal=0.5):
+    n = len(p)
+    e = {f: np.full(n, math.nan) for f in E.FIELDS}
+    e["p_lognormal"], e["var_lw"], e["count"] = np.array(p, float), np.array(var, float), np.array(count, float)
+    e["p_normal"] = np.full(n, p_normal)
+    e["p_direct"] = np.array(p, float)
+    e["se_direct"] = np.array(p, float) * 0.1
+    return e
+
+
+def test_stitch_hand_example_and_filters():
+    """Two simulations of one bin: relative errors a1 = 0.1, a2 = 0.2 (set up
+    through var and count with the count term included) -> weights 100 and 25,
+    ln p = (100 ln 1e-10 + 25 ln 2e-10) / 125 -> p = 1e-10 * 2^0.2, a = 1/sqrt(125)."""
+    n = 10000.0
+    # choose var so that var/n + var^2/(2n - 2) + 1/n = a^2
+    def var_for(a):
+        c = 1.0 / (2 * n - 2)
+        return (-1.0 / n + math.sqrt(1.0 / n ** 2 + 4 * c * (a * a - 1.0 / n))) / (2 * c)
+    e1 = _fake_estimate([1e-10], [var_for(0.1)], [n])
+    e2 = _fake_estimate([2e-10], [var_for(0.2)], [n])
+    o = E.stitch([e1, e2])
+    assert math.isclose(o["p"][0], 1e-10 * 2 ** 0.2, rel_tol=1e-12)
+    assert math.isclose(o["log_err"][0], 1 / math.sqrt(125), rel_tol=1e-12)
+    assert o["n_used"][0] == 2 and o["best"][0] == 0
+    # a single simulation is returned as it is
+    o1 = E.stitch([e1])
+    assert math.isclose(o1["p"][0], 1e-10, rel_tol=1e-14) and math.isclose(o1["log_err"][0], 0.1, rel_tol=1e-12)
+    # filters: too few runs, failed normality, nothing left
+    assert E.stitch([_fake_estimate([1e-10], [0.5], [399])])["n_used"][0] == 0
+    assert math.isnan(E.stitch([_fake_estimate([1e-10], [0.5], [1000], p_normal=0.001)])["p"][0])
+    o2 = E.stitch([e1, _fake_estimate([5e-10], [0.5], [1000], p_normal=0.001)])
+    assert o2["n_used"][0] == 1 and math.isclose(o2["p"][0], 1e-10, rel_tol=1e-14)
+    # w = 1 in the bin: zero variance, no normality test, kept with the count's error 1/sqrt(n)
+    o3 = E.stitch([_fake_estimate([3e-3], [0.0], [2500], p_normal=math.nan)])
+    assert o3["n_used"][0] == 1 and math.isclose(o3["log_err"][0], 1 / 50, rel_tol=1e-12)
+    od = E.stitch([e1, e2], estimator="direct")
+    assert math.isclose(od["p"][0], math.sqrt(1e-10 * 2e-10), rel_tol=1e-12)  # equal relative errors
+
+
+def test_stitch_error_covers_the_truth():
+    """K simulations of the same lognormal bin: the combined estimate's interval
+    covers the true mean about 68 % of the time."""
+    rng = np.random.default_rng(5)
+    mu, sig, reps = -5.0, 1.2, 300
+    truth = math.exp(mu + sig * sig / 2)
+    hit = 0
+    for r in range(reps):
+        ests = []
+        for k in range(4):
+            n = int(rng.integers(400, 2000))
+            lw = rng.normal(mu, sig, n)
+            ests.append(E.estimate(np.full(n, 0.5), lw, 1, 0.0, 1.0))
+            # a bin holding all n runs of n_total = n: P = <w> exactly as Eq. (23) with n_j = n_total
+        o = E.stitch(ests, p_threshold=0.0)
+        hit += (o["p"][0] - o["eps_lo"][0] <= truth <= o["p"][0] + o["eps_hi"][0])
+    assert 0.58 <= hit / reps <= 0.80, hit / reps
