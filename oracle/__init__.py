@@ -14,7 +14,10 @@ Parity status of each function (what pins it is listed in the tests):
                      b = 0, the brute-force path likelihood ratio; power-law
                      bias (§3.5 Eq. (26)): p = 1 equals the constant bias,
                      path likelihood ratio for p = 0, 2.5, 3, backward-equation
-                     mean with drift D + A phi^3, E[w] = 1, classical duration
+                     mean with drift D + A phi^3, E[w] = 1, classical duration;
+                     polynomial potential (§2.3 Eq. (17)): c2 = m^2/2 equals the
+                     quadratic model, backward-equation moments of a quartic and
+                     a phi^2 + phi^4 potential, E[w] = 1
   histogram          pinned: brute-force binning with numpy.digitize; moments
                      of ln w - max_lw against numpy mean / var
   estimate (module)  pinned: scipy.stats normaltest / skewtest / kurtosistest;
@@ -34,6 +37,8 @@ from . import build as _build
 
 MODEL_QUADRATIC = 0
 MODEL_CONSTANT = 1
+MODEL_POLYNOMIAL = 2
+POLY_TERMS = 8
 BIAS_CONST = 0
 BIAS_POWER = 1
 BIAS_MLP = 2
@@ -61,6 +66,7 @@ class OracleRun(ctypes.Structure):
         ("mlp_norm", ctypes.c_double * 4),
         ("k_eval", ctypes.c_int32),
         ("bias_p", ctypes.c_double),
+        ("poly", ctypes.c_double * 8),
     ]
 
 
@@ -99,9 +105,10 @@ def _ptr(a, ct):
 
 def make_run(*, model=MODEL_QUADRATIC, m=1.0, a0=0.0, s0=0.0, phi_in, phi_end=math.sqrt(2.0),
              phi_uv=math.inf, dN, b=0.0, n_max, seed=0, set_id=0, traj_offset=0, mlp=None,
-             mlp_norm=(0.0, 1.0, 0.0, 1.0), k_eval=1, bias_p=None):
+             mlp_norm=(0.0, 1.0, 0.0, 1.0), k_eval=1, bias_p=None, poly=None):
     """One parameter set.  b is the amplitude of B = b S(phi), or, with bias_p
-    given, of the power law B = b phi^bias_p (§3.5 Eq. (26))."""
+    given, of the power law B = b phi^bias_p (§3.5 Eq. (26)).  poly: the
+    coefficients c_k of V = sum_k c_k phi^k for model=MODEL_POLYNOMIAL."""
     r = OracleRun()
     r.model, r.m, r.a0, r.s0 = model, m, a0, s0
     r.phi_in, r.phi_end, r.phi_uv = phi_in, phi_end, phi_uv
@@ -110,6 +117,9 @@ def make_run(*, model=MODEL_QUADRATIC, m=1.0, a0=0.0, s0=0.0, phi_in, phi_end=ma
     r.bias_kind = BIAS_CONST
     r.mlp_norm = (ctypes.c_double * 4)(*mlp_norm)
     r.k_eval = k_eval
+    if poly is not None:
+        c = list(poly) + [0.0] * (POLY_TERMS - len(poly))
+        r.poly = (ctypes.c_double * POLY_TERMS)(*c[:POLY_TERMS])
     if bias_p is not None:
         r.bias_kind = BIAS_POWER
         r.bias_p = bias_p

@@ -77,17 +77,35 @@ void oracle_normals4(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k, 
 /* (§1 Eqs. (3)-(4), §2.3 Eq. (17)) for V = m^2 phi^2 / 2 (§3 Eq. (25)),     */
 /* M_Pl = 1:  H^2 = V/3,  D = -V'/(3 H^2),  S = H / (2 pi).                  */
 /* ------------------------------------------------------------------------ */
+/* V(phi) and dV/dphi of the polynomial model, by Horner's rule from the top term. */
+static double poly_V(const oracle_run* r, double phi) {
+    double v = 0.0;
+    for (int k = ORACLE_POLY_TERMS - 1; k >= 0; --k) v = v * phi + r->poly[k];
+    return v;
+}
+static double poly_dV(const oracle_run* r, double phi) {
+    double v = 0.0;
+    for (int k = ORACLE_POLY_TERMS - 1; k >= 1; --k) v = v * phi + (double)k * r->poly[k];
+    return v;
+}
+
 static double drift(const oracle_run* r, double phi) {
     if (r->model == ORACLE_MODEL_CONSTANT) return r->a0;
-    double V = 0.5 * r->m * r->m * phi * phi;
-    double dV = r->m * r->m * phi;
+    double V, dV;
+    if (r->model == ORACLE_MODEL_POLYNOMIAL) {
+        V = poly_V(r, phi);
+        dV = poly_dV(r, phi);
+    } else {
+        V = 0.5 * r->m * r->m * phi * phi;
+        dV = r->m * r->m * phi;
+    }
     double H2 = V / 3.0;
     return -dV / (3.0 * H2);
 }
 
 static double noise(const oracle_run* r, double phi) {
     if (r->model == ORACLE_MODEL_CONSTANT) return r->s0;
-    double V = 0.5 * r->m * r->m * phi * phi;
+    double V = r->model == ORACLE_MODEL_POLYNOMIAL ? poly_V(r, phi) : 0.5 * r->m * r->m * phi * phi;
     double H = sqrt(V / 3.0);
     return H / (2.0 * M_PI);
 }
@@ -159,6 +177,9 @@ static int run_valid(const oracle_run* r) {
         if (!(r->m > 0.0) || !(r->phi_end > 0.0)) return 0;
     } else if (r->model == ORACLE_MODEL_CONSTANT) {
         if (!(r->s0 > 0.0)) return 0;
+    } else if (r->model == ORACLE_MODEL_POLYNOMIAL) {
+        /* the potential must be positive where runs start and end */
+        if (!(poly_V(r, r->phi_in) > 0.0) || !(poly_V(r, r->phi_end) > 0.0)) return 0;
     } else {
         return 0;
     }

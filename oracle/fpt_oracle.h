@@ -25,6 +25,8 @@ extern "C" {
 /* Models (drift D and noise amplitude S of the Langevin equation, §2.1 Eq. (7)). */
 #define ORACLE_MODEL_QUADRATIC 0 /* §3 Eq. (25) with §2.3 Eq. (17): D = -2/phi, S = m phi / (2 pi sqrt 6) */
 #define ORACLE_MODEL_CONSTANT 1  /* test model: D = a0, S = s0 (constant drift and noise) */
+#define ORACLE_MODEL_POLYNOMIAL 2 /* V = sum_k poly[k] phi^k, D = -V'/(3 H^2), H^2 = V/3, S = H/(2 pi) (§2.3 Eq. (17)) */
+#define ORACLE_POLY_TERMS 8
 
 /* Bias kinds (§2.3 Eq. (18): B = A f(phi)). */
 #define ORACLE_BIAS_CONST 0 /* B = b S(phi): f = S, A = b */
@@ -53,6 +55,8 @@ typedef struct {
     int32_t k_eval;     /* bias is re-evaluated at steps m = 0, k_eval, 2 k_eval, ... */
     /* power-law bias only */
     double bias_p;      /* exponent p of B = b phi^p */
+    /* polynomial model only */
+    double poly[ORACLE_POLY_TERMS]; /* V(phi) = sum_k poly[k] phi^k */
 } oracle_run;
 
 /* Philox4x32-10 block function: out = Philox(ctr, key), 10 rounds. */

@@ -292,3 +292,46 @@ def test_power_bias_drift_dominated_classical_duration():
     ncl = integrate.quad(lambda x: 1.0 / (2.0 / x - amp * x ** p), SQ2, 6.0, epsabs=1e-12, epsrel=1e-12)[0]
     assert ncl > 8.6  # the bias lengthens inflation by several sigma_N ~ 0.02
     assert abs(N.mean() / ncl - 1) < 5e-4
+
+
+# ---- general potential V(phi) = sum_k c_k phi^k (§2.3 Eq. (17)) ----
+
+def _poly_fns(c):
+    """D = -V'/V and S = sqrt(V/3)/(2 pi) of the polynomial potential, numpy."""
+    P = np.polynomial.Polynomial(c)
+    dP = P.deriv()
+    return (lambda x: -dP(x) / P(x)), (lambda x: np.sqrt(P(x) / 3.0) / (2 * math.pi))
+
+
+def test_polynomial_model_reduces_to_quadratic():
+    m = 0.7
+    a = oracle.simulate(oracle.make_run(m=m, phi_in=3.0, phi_uv=3.5, dN=1e-3, b=0.7, n_max=6.0), 300)
+    b = oracle.simulate(oracle.make_run(model=oracle.MODEL_POLYNOMIAL, poly=[0, 0, 0.5 * m * m], phi_in=3.0,
+                                        phi_uv=3.5, dN=1e-3, b=0.7, n_max=6.0), 300)
+    assert np.array_equal(a[2], b[2])
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-12)
+    np.testing.assert_allclose(b[1], a[1], rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("c,phi_in,phi_end,phi_uv,b", [
+    ([0, 0, 0, 0, 0.25 * 0.05], 4.0, math.sqrt(8.0), 4.6, 0.0),         # quartic lambda phi^4 / 4
+    ([0, 0, 0.5 * 0.3, 0, 0.25 * 0.02], 3.5, 1.6, 4.0, 0.5),            # phi^2 + phi^4 mix, biased
+])
+def test_polynomial_model_moments_and_weights(c, phi_in, phi_end, phi_uv, b):
+    """<N> and Var N of the sample process from the backward equations with
+    D + b S, and E[w] = 1 with the weighted mean equal to the unbiased one."""
+    n, dN = 6000, 1e-3
+    r = oracle.make_run(model=oracle.MODEL_POLYNOMIAL, poly=c, phi_in=phi_in, phi_end=phi_end, phi_uv=phi_uv, dN=dN,
+                        b=b, n_max=200.0)
+    N, lw, _ = oracle.simulate(r, n)
+    assert np.all(np.isfinite(N))
+    D, S = _poly_fns(c)
+    ms, vs = A.backward_moments_fd(phi_in, lambda x: D(x) + b * S(x), S, phi_end, phi_uv)
+    assert abs(N.mean() - ms) < 4 * math.sqrt(vs / n) + 3e-3 * ms
+    assert abs(N.var() / vs - 1) < 4 * math.sqrt(2.0 / n) * 2
+    w = np.exp(lw)
+    assert abs(w.mean() - 1.0) < 4 * w.std() / math.sqrt(n) + 1e-12
+    mt, _ = A.backward_moments_fd(phi_in, D, S, phi_end, phi_uv)
+    est = np.sum(w * N) / np.sum(w)
+    se = math.sqrt(np.mean((w * (N - est)) ** 2) / n) / np.mean(w)
+    assert abs(est - mt) < 4 * se + 3e-3 * mt
