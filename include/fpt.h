@@ -65,6 +65,9 @@ extern "C" {
 /* drift/noise model */
 #define FPT_MODEL_QUADRATIC 0 /* D = -2/phi, S = m phi/(2 pi sqrt 6): §2.3 Eq. (17) + §3 Eq. (25) */
 #define FPT_MODEL_CONSTANT 1  /* D = a0, S = s0: constant drift and noise (inverse-Gaussian test model) */
+#define FPT_MODEL_POLYNOMIAL 2 /* V(phi) = sum_k poly[k] phi^k (M_Pl = 1): D = -V'/(3 H^2), H^2 = V/3,
+                                  S = H/(2 pi) (§2.3 Eq. (17)); V must be positive wherever runs go */
+#define FPT_POLY_TERMS 8
 
 /* arithmetic of the stepper */
 #define FPT_PREC_F64 0        /* everything binary64 (reference mode, per-run parity with the FP64 oracle) */
@@ -88,6 +91,7 @@ typedef struct fpt_params {
     double a0, s0;       /* constant model: drift and noise amplitude (s0 > 0) */
     double n_max;        /* censoring time, finite and > 0 */
     double bias_p;       /* FPT_BIAS_POWER: exponent p (finite; integers 0..4 have specialised kernels) */
+    double poly[FPT_POLY_TERMS]; /* FPT_MODEL_POLYNOMIAL: coefficients of V (the sets' m is ignored) */
     const void* mlp;     /* FPT_BIAS_MLP: device pointer to an fpt_mlp_params */
     int32_t k_eval;      /* FPT_BIAS_MLP: steps between bias evaluations (0 = 32) */
     int32_t block_dim;   /* threads per block of the stepper (0 = autotuned or default) */

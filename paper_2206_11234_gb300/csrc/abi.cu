@@ -61,8 +61,16 @@ int check_params(const fpt_params* p) {
     if (!p) return fail(FPT_EINVAL, "params is NULL");
     if (p->abi_version != FPT_ABI_VERSION)
         return fail(FPT_EINVAL, "abi_version %d, library is %d", p->abi_version, FPT_ABI_VERSION);
-    if (p->model != FPT_MODEL_QUADRATIC && p->model != FPT_MODEL_CONSTANT)
+    if (p->model != FPT_MODEL_QUADRATIC && p->model != FPT_MODEL_CONSTANT && p->model != FPT_MODEL_POLYNOMIAL)
         return fail(FPT_EINVAL, "unknown model %d", p->model);
+    if (p->model == FPT_MODEL_POLYNOMIAL) {
+        bool any = false;
+        for (int k = 0; k < FPT_POLY_TERMS; ++k) {
+            if (!std::isfinite(p->poly[k])) return fail(FPT_EINVAL, "poly[%d] is not finite", k);
+            any = any || p->poly[k] != 0.0;
+        }
+        if (!any) return fail(FPT_EINVAL, "the polynomial potential is zero");
+    }
     if (p->precision != FPT_PREC_F64 && p->precision != FPT_PREC_F32_KAHAN &&
         p->precision != FPT_PREC_F32_F64ACC)
         return fail(FPT_EINVAL, "unknown precision %d", p->precision);
@@ -95,6 +103,17 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
     if (!std::isfinite(s.b)) return fail(FPT_EINVAL, "bias must be finite");
     if (p->model == FPT_MODEL_QUADRATIC && !(s.m > 0.0 && std::isfinite(s.m) && s.phi_end > 0.0))
         return fail(FPT_EINVAL, "quadratic model needs m > 0 and phi_end > 0");
+    if (p->model == FPT_MODEL_POLYNOMIAL) {
+        auto V = [&](double x) {
+            double v = 0.0;
+            for (int k = FPT_POLY_TERMS - 1; k >= 0; --k) v = v * x + p->poly[k];
+            return v;
+        };
+        if (!(V(s.phi_in) > 0.0) || !(V(s.phi_end) > 0.0))
+            return fail(FPT_EINVAL, "the potential must be positive at phi_in and phi_end");
+        if (std::isfinite(s.phi_uv) && !(V(s.phi_uv) > 0.0))
+            return fail(FPT_EINVAL, "the potential must be positive at the wall");
+    }
     const double steps = std::ceil(s.n_max / s.dN);
     if (!(steps <= 2147483647.0 - 64.0))
         return fail(FPT_EINVAL, "n_max/dN = %g steps exceeds the 2^31 step limit", steps);
@@ -134,6 +153,17 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
         c.f_pm1 = (float)(p->bias_p - 1.0);
         c.f_pw1 = (float)(-s.b / (c.cm * c.cm));
         c.f_pw2 = (float)(-0.5 * s.b * s.b * s.dN / (c.cm * c.cm));
+    } else if (p->model == FPT_MODEL_POLYNOMIAL) {
+        // dphi = S (b dN + sqrt(dN) xi) + D dN with D = -V'/V and S = sqrt(V) / (2 pi sqrt 3)
+        c.cm = 0.0;
+        for (int k = 0; k < FPT_POLY_TERMS; ++k) {
+            c.poly[k] = p->poly[k];
+            c.f_poly[k] = (float)p->poly[k];
+            c.f_dpoly[k] = k + 1 < FPT_POLY_TERMS ? (float)((double)(k + 1) * p->poly[k + 1]) : 0.0f;
+        }
+        c.f_c1 = (float)(s.b * s.dN);                        // bias part of dphi / S
+        c.f_c2 = (float)(neg_sqrt2ln2 * c.sq);               // noise part of dphi / S per unit rho cos
+        c.f_c3 = (float)s.dN;
     } else if (p->model == FPT_MODEL_QUADRATIC) {
         c.f_c1 = (float)(s.b * c.cm * s.dN);                 // bias part of dphi/phi
         c.f_c2 = (float)(neg_sqrt2ln2 * c.cm * c.sq);        // noise part of dphi/phi per unit rho cos

@@ -31,7 +31,7 @@ namespace {
 constexpr size_t kScratchHeader = 256;  // StepperScratch, padded to the set table's alignment
 constexpr size_t kNoAllocBytes = kScratchHeader + FPT_NOALLOC_MAX_SETS * sizeof(SetConst);
 static_assert(sizeof(StepperScratch) <= kScratchHeader, "scratch header");
-static_assert(kNoAllocBytes <= 12288, "the no-alloc scratch stays modest");
+static_assert(kNoAllocBytes <= 16384, "the no-alloc scratch stays modest");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -88,6 +88,36 @@ struct ModelStep<float, FPT_MODEL_CONSTANT> {
     __device__ __forceinline__ float step(float phi, float t) const { return __fadd_rn(phi, t); }
 };
 
+// Polynomial potential V = sum_k c_k phi^k (§2.3 Eq. (17), M_Pl = 1), binary32:
+// D = -V'/V and S = sqrt(V) / (2 pi sqrt 3), and the step is
+// dphi = S t + D dN with t = b dN + sqrt(dN) xi (so the bias is B = b S).  The
+// coefficients are read from the set table in shared memory.
+template <>
+struct ModelStep<float, FPT_MODEL_POLYNOMIAL> {
+    float tc, kq, dN;   // tc = b dN, kq = -sqrt(2 ln 2) sqrt(dN), dN
+    const float* c;     // V
+    const float* dc;    // V'
+    __device__ __forceinline__ void load(const SetConst& s) {
+        tc = s.f_c1;
+        kq = s.f_c2;
+        dN = s.f_c3;
+        c = s.f_poly;
+        dc = s.f_dpoly;
+    }
+    __device__ __forceinline__ float step(float phi, float t) const {
+        constexpr float kS = 0.091888149f;  // 1 / (2 pi sqrt 3)
+        float v = c[FPT_POLY_TERMS - 1], dv = dc[FPT_POLY_TERMS - 1];
+#pragma unroll
+        for (int k = FPT_POLY_TERMS - 2; k >= 0; --k) {
+            v = __fmaf_rn(v, phi, c[k]);
+            dv = __fmaf_rn(dv, phi, dc[k]);
+        }
+        const float S = __fmul_rn(kS, sqrt_approx(v));
+        const float D = -__fmul_rn(dv, rcp_approx(v));
+        return __fadd_rn(phi, __fmaf_rn(S, t, __fmul_rn(D, dN)));
+    }
+};
+
 // Quadratic potential with B = A_p phi^p, binary32.  With u = phi^(p-1):
 // dphi = phi t - 2 dN / phi, t = A_p dN u + c m sqrt(dN) xi, and the step's
 // log-weight -beta sqrt(dN) xi - beta^2 dN / 2 with beta = B/S = (A_p / c m) u,
@@ -205,6 +235,31 @@ struct ModelStep<double, FPT_MODEL_CONSTANT> {
     }
     __device__ __forceinline__ double step(double phi, double xi) const {
         return phi + (a0 + b * s0) * dN + s0 * xi * sq;
+    }
+};
+
+// Polynomial potential, binary64: V and V' by Horner's rule from the top term,
+// D = -V'/(3 H^2) with H^2 = V/3 and S = sqrt(V/3) / (2 pi), as written in §2.3
+// Eq. (17); the update of Eq. (11) with B = b S.
+template <>
+struct ModelStep<double, FPT_MODEL_POLYNOMIAL> {
+    double b, dN, sq;
+    const double* c;
+    __device__ __forceinline__ void load(const SetConst& s) {
+        b = s.b;
+        dN = s.dN;
+        sq = s.sq;
+        c = s.poly;
+    }
+    __device__ __forceinline__ double step(double phi, double xi) const {
+        double V = 0.0, dV = 0.0;
+        for (int k = FPT_POLY_TERMS - 1; k >= 0; --k) V = V * phi + c[k];
+        for (int k = FPT_POLY_TERMS - 1; k >= 1; --k) dV = dV * phi + (double)k * c[k];
+        const double H2 = V / 3.0;
+        const double D = -dV / (3.0 * H2);
+        const double S = sqrt(V / 3.0) / (2.0 * 3.14159265358979323846);
+        const double B = b * S;
+        return phi + (D + B) * dN + S * xi * sq;
     }
 };
 

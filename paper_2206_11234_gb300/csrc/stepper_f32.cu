@@ -37,6 +37,7 @@ template <int PREC>
 StepperKernel by_model(int model, bool wall, int ks) {
     if (model == FPT_MODEL_QUADRATIC) return by_wall<PREC, FPT_MODEL_QUADRATIC>(wall, ks);
     if (model == FPT_MODEL_CONSTANT) return by_wall<PREC, FPT_MODEL_CONSTANT>(wall, ks);
+    if (model == FPT_MODEL_POLYNOMIAL) return by_wall<PREC, FPT_MODEL_POLYNOMIAL>(wall, ks);
     return StepperKernel{nullptr, 0, nullptr};
 }
 

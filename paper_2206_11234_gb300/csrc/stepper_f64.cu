@@ -40,6 +40,7 @@ StepperKernel by_wall(bool wall, int ks) {
 StepperKernel stepper_f64(int model, bool wall, int k_steps) {
     if (model == FPT_MODEL_QUADRATIC) return by_wall<FPT_MODEL_QUADRATIC>(wall, k_steps);
     if (model == FPT_MODEL_CONSTANT) return by_wall<FPT_MODEL_CONSTANT>(wall, k_steps);
+    if (model == FPT_MODEL_POLYNOMIAL) return by_wall<FPT_MODEL_POLYNOMIAL>(wall, k_steps);
     if (model == kModelPowReal) return by_wall<kModelPowReal>(wall, k_steps);
     return StepperKernel{nullptr, 0, nullptr};
 }

@@ -36,6 +36,10 @@ struct SetConst {
     // weight constants of ModelStep for the power models (stepper.cuh)
     double pw;
     float f_pm1, f_pw1, f_pw2;              // p - 1, -A_p/(c m)^2, -A_p^2 dN/(2 (c m)^2)
+    // polynomial potential V = sum_k poly[k] phi^k: binary64 coefficients, and
+    // binary32 coefficients of V and V' (f_dpoly[k] = (k + 1) poly[k + 1])
+    double poly[FPT_POLY_TERMS];
+    float f_poly[FPT_POLY_TERMS], f_dpoly[FPT_POLY_TERMS];
 };
 
 // Bytes of the per-set table at the start of the stepper's dynamic shared

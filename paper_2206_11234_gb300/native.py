@@ -26,6 +26,8 @@ FPT_EDEVICE_STATUS = -5
 
 MODEL_QUADRATIC = 0
 MODEL_CONSTANT = 1
+MODEL_POLYNOMIAL = 2
+POLY_TERMS = 8
 PREC_F64 = 0
 PREC_F32_KAHAN = 1
 PREC_F32_F64ACC = 2
@@ -48,6 +50,7 @@ class FptParams(ctypes.Structure):
         ("s0", ctypes.c_double),
         ("n_max", ctypes.c_double),
         ("bias_p", ctypes.c_double),
+        ("poly", ctypes.c_double * 8),
         ("mlp", ctypes.c_void_p),
         ("k_eval", ctypes.c_int32),
         ("block_dim", ctypes.c_int32),
@@ -187,10 +190,11 @@ def _stream(stream) -> Optional[int]:
 def make_params(*, model=MODEL_QUADRATIC, precision=PREC_F64, m=1.0, a0=0.0, s0=0.0, n_max,
                 block_dim=0, k_steps=0, set_id=0, traj_offset=0, stream=None,
                 steps_out: Optional[torch.Tensor] = None, mlp: Optional[torch.Tensor] = None,
-                k_eval: int = 0, bias_p: Optional[float] = None) -> FptParams:
+                k_eval: int = 0, bias_p: Optional[float] = None, poly=None) -> FptParams:
     """Launch parameters.  The bias is B = b S (the sets' b) by default, the
     power law B = b phi^bias_p when bias_p is given, the learned b(phi, N) S
-    when mlp is given."""
+    when mlp is given.  poly: coefficients c_0.. of V = sum_k c_k phi^k for
+    model=MODEL_POLYNOMIAL (at most POLY_TERMS)."""
     p = FptParams()
     p.abi_version = FPT_ABI_VERSION
     p.model = model
@@ -202,6 +206,11 @@ def make_params(*, model=MODEL_QUADRATIC, precision=PREC_F64, m=1.0, a0=0.0, s0=
         p.bias_kind = BIAS_POWER
         p.bias_p = bias_p
     p.m, p.a0, p.s0, p.n_max = m, a0, s0, n_max
+    if poly is not None:
+        c = [float(x) for x in poly]
+        if len(c) > POLY_TERMS:
+            raise ValueError(f"at most {POLY_TERMS} coefficients")
+        p.poly = (ctypes.c_double * POLY_TERMS)(*(c + [0.0] * (POLY_TERMS - len(c))))
     p.mlp = None if mlp is None else mlp.data_ptr()
     p.k_eval = k_eval
     p.block_dim, p.k_steps = block_dim, k_steps

@@ -108,6 +108,13 @@ def test_host_side_argument_checks(native):
     assert sim(_params(native, n_max=0.0)) == E
     assert sim(_params(native, n_max=1e9)) == E  # beyond 2^31 steps
     assert sim(_params(native, m=0.0)) == E
+    # polynomial potential: zero, non-finite, or non-positive where runs start
+    assert sim(_params(native, model=native.MODEL_POLYNOMIAL)) == E
+    pp = _params(native, model=native.MODEL_POLYNOMIAL)
+    pp.poly[2] = math.nan
+    assert sim(pp) == E
+    pp.poly[2] = -1.0
+    assert sim(pp) == E
     assert b"dN" in L.fpt_last_error() or len(L.fpt_last_error()) > 0
     # n_traj = 0 is a no-op that needs no GPU
     assert sim(_params(native), n=0, out=None) == native.FPT_OK
