@@ -52,11 +52,12 @@ def stepper_source_hash() -> str:
     return h.hexdigest()
 
 
-def stepper_traffic(precision, block_dim, k_steps, runs):
-    """DRAM bytes (read + write) of one stepper launch over `runs` runs, scaled
-    from the ncu capture recorded in profiles/stepper_dram_traffic.json; None
-    when no capture matches this kernel, launch shape and source."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "stepper_dram_traffic.json")
+def stepper_counters(precision, block_dim, k_steps):
+    """The ncu counters recorded for the binary32 stepper in
+    profiles/stepper_counters.json (DRAM bytes, instructions, branch and lane
+    efficiency of one launch over a stated number of runs and steps), or None
+    when no record matches this kernel, launch shape and source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "stepper_counters.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -66,7 +67,7 @@ def stepper_traffic(precision, block_dim, k_steps, runs):
         return None
     if rec.get("source_sha256") != stepper_source_hash():
         return None
-    return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * runs / rec["runs"]
+    return rec
 
 
 def parse():
@@ -713,10 +714,21 @@ def main():
     steps_peak = min(issue_peak / ALG_INST_PER_STEP, n_sm * MUFU_PER_SM_CLK * f_max / MUFU_PER_STEP) * 32
     achieved_steps = stepper_steps / (ms_stepper / 1e3)
     shape = tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}
+    ctr = stepper_counters(wl.precision, shape.get("block_dim"), shape.get("k_steps"))
+    measured = None
+    if ctr:
+        inst_ws = ctr["inst_executed"] / (ctr["steps"] / 32.0)  # warp-instructions per warp-step
+        measured = {"inst_per_warp_step": inst_ws,
+                    "steps_per_s_peak": issue_peak / inst_ws * 32,
+                    "frac": achieved_steps / (issue_peak / inst_ws * 32),
+                    "branch_targets_uniform_pct": ctr["branch_targets_uniform_pct"],
+                    "active_lanes_per_inst_pct": 100.0 * ctr["thread_inst_executed"] / (32.0 * ctr["inst_executed"]),
+                    "source": "profiles/stepper_counters.json"}
     roof = {"bound": "alu", "achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9,
             "peak": issue_peak / 1e9, "unit": "Gwarp-inst/s (algorithmic)",
             "frac": achieved_steps / steps_peak,
-            "traffic": stepper_traffic(wl.precision, shape.get("block_dim"), shape.get("k_steps"), n),
+            "traffic": (ctr["dram_read_bytes"] + ctr["dram_write_bytes"]) * n / ctr["runs"] if ctr else None,
+            "vs_measured_instructions": measured,
             "kernel": f"stepper_kernel<float, {wl.precision}, quadratic, "
                       f"k_steps {(tuned or {}).get('k_steps', args.k_steps)}>",
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
@@ -725,13 +737,16 @@ def main():
     cpu = None
     if not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+        rate1, _, sample1 = cpu_oracle_rate(wl, min(3.0, args.cpu_seconds), threads=1)
+        cpu = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": rate1, "sample": sample1}}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl.precision != "f64" else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "precision": wl.precision, "runs_per_gpu": n,
+                   "em_steps_per_step": total_steps / args.steps,
                    "sets": len(specs), "l2": "outputs (16 B/run) exceed L2; no inputs besides parameters",
                    "parallelism": f"dp{world} (disjoint run ids per GPU)",
                    "launch_shape": tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}},
@@ -741,6 +756,8 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "context": "the paper's CPU package (Python) reports ~8 h for 2e5 drift-dominated runs on a quad-core "
+                   "laptop and 'a few hours on a single CPU' for the whole study; it gives no steps/s",
     }
     line.update(extra)
     print(json.dumps(line))
