@@ -63,7 +63,8 @@ def stepper_counters(precision, block_dim, k_steps):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if (rec.get("precision"), rec.get("block_dim"), rec.get("k_steps")) != (precision, block_dim, k_steps):
+    # the executed code depends on the precision and block length, not on the block size
+    if (rec.get("precision"), rec.get("k_steps")) != (precision, k_steps):
         return None
     if rec.get("source_sha256") != stepper_source_hash():
         return None

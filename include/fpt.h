@@ -339,7 +339,8 @@ int fpt_mlp_backward(const fpt_mlp_params* w, const float* phi, const float* N, 
                      float* grad, void* stream);
 
 /* Autotuner of the stepper's launch shape (threads per block in {128, 256, 512}
- * and steps per scheduling block k_steps in {8, 16, 32}, binary64: {4, 8}).
+ * and steps per scheduling block k_steps in {8, 16, 32, 64}, binary64: {4, 8};
+ * the binary32 power-law bias kernels exist for 32 only).
  * Runs pilot launches over the given sets with each n_traj scaled by
  * `fraction` in (0, 1] (raised if needed so the pilot fills the GPU), times
  * each shape with CUDA events on p->stream and keeps the fastest in EM steps

@@ -87,10 +87,12 @@ extern "C" int fpt_autotune(const fpt_params* p, const fpt_set* sets, int32_t n_
     cudaEventCreate(&e1);
 
     const int blocks[3] = {128, 256, 512};
-    const int ks32[3] = {8, 16, 32};
-    const int ks64[2] = {4, 8};
-    const int* kss = p->precision == FPT_PREC_F64 ? ks64 : ks32;
-    const int nks = p->precision == FPT_PREC_F64 ? 2 : 3;
+    const int ks32[4] = {8, 16, 32, 64};  // binary32 block lengths
+    const int ks64[2] = {4, 8};           // binary64
+    const int ks_pow[1] = {32};          // binary32 power-law bias kernels
+    const bool pw = p->bias_kind == FPT_BIAS_POWER && p->precision != FPT_PREC_F64;
+    const int* kss = p->precision == FPT_PREC_F64 ? ks64 : (pw ? ks_pow : ks32);
+    const int nks = p->precision == FPT_PREC_F64 ? 2 : (pw ? 1 : 4);
     double best = -1.0;
     int best_b = 256, best_k = kss[0];
     fpt_params q = *p;

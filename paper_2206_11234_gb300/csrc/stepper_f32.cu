@@ -24,6 +24,7 @@ StepperKernel by_ks(int ks) {
         case 8: return make<PREC, MODEL, WALL, 8>();
         case 16: return make<PREC, MODEL, WALL, 16>();
         case 32: return make<PREC, MODEL, WALL, 32>();
+        case 64: return make<PREC, MODEL, WALL, 64>();
         default: return StepperKernel{nullptr, 0, nullptr};
     }
 }

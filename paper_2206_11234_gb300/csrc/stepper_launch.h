@@ -17,7 +17,7 @@ inline size_t stepper_smem(const StepperKernel& k, int block, int n_sets) {
     return stepper_table_bytes(n_sets) + (size_t)(block / 32) * (size_t)k.warp_smem_bytes;
 }
 
-// Block lengths with an instantiation: binary32 8/16/32, binary64 4/8; the
+// Block lengths with an instantiation: binary32 8/16/32/64, binary64 4/8; the
 // power-law bias (model = kModelPowReal in binary64): binary32 32, binary64 4/8.
 StepperKernel stepper_f32(int precision, int model, bool wall, int k_steps);
 StepperKernel stepper_f64(int model, bool wall, int k_steps);
