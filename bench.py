@@ -735,6 +735,13 @@ def main():
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
             "peak_source": f"{n_sm} SMs x 4 issue/clk x {f_max / 1e6:.0f} MHz (max SM clock, "
                            "MEASURED_PEAKS.json); MUFU co-bound 16/clk/SM"}
+    if wl.precision == "f64":
+        # the binary64 reference path (per-run parity configuration): no FP64 peak
+        # is measured on this machine and the FP32 issue roofline does not apply
+        roof = {"bound": "fp64", "achieved": achieved_steps, "peak": None, "unit": "steps/s", "frac": None,
+                "traffic": None, "kernel": f"stepper_kernel<double, f64, {wl.sets[0].model and 'constant' or 'quadratic'}, "
+                                           f"k_steps {shape.get('k_steps')}>",
+                "note": "binary64 reference path; no roofline fraction is claimed"}
     cpu = None
     if not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
