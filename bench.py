@@ -377,7 +377,7 @@ def run_estimators(args):
 
 
 def run_power_bias(args):
-    """The bias-optimisation experiment of §3.5: quadratic inflation m = 0.001,
+    """The bias-optimisation experiment of §3.4: quadratic inflation m = 0.001,
     phi_in = 6 (drift domination), B = A_p phi^p for p = 0 .. 5 with A_p tuned
     so that the classical sample duration sits 8 classical sigma_N past the
     target's; dN = 1e-4 (sigma_N / 20); 2^18 runs per p (binary32 state,

@@ -76,7 +76,7 @@ extern "C" {
 
 /* bias of the sample process (§2.3 Eq. (18)) */
 #define FPT_BIAS_CONST 0 /* B = b S(phi), b constant (the set's bias) */
-#define FPT_BIAS_POWER 1 /* B = A_p phi^p (§3.5 Eq. (26)), A_p = the set's bias, p = bias_p; quadratic model */
+#define FPT_BIAS_POWER 1 /* B = A_p phi^p (§3.4 Eq. (26)), A_p = the set's bias, p = bias_p; quadratic model */
 #define FPT_BIAS_MLP 2   /* B = b S, b = MLP(phi, N_elapsed), held for k_eval steps (see fpt_mlp_params) */
 
 #define FPT_MAX_SETS 64       /* parameter sets per batched launch */
@@ -258,7 +258,7 @@ int fpt_stitch(const fpt_estimate_bin* est, int32_t n_runs, int32_t n_bins, int3
                double p_threshold, fpt_stitch_bin* out, void* stream);
 
 /* Pearson's correlation coefficient of (N_i, ln w_i) over the runs with finite
- * N_i (§3.5: |r| of log10 w with N measures how tightly the (N, w) cloud is
+ * N_i (§3.4: |r| of log10 w with N measures how tightly the (N, w) cloud is
  * squeezed and guides the choice of the bias; log10 w and ln w differ by a
  * constant factor, which r does not see).  N, logw: device double[n].  Two
  * passes in binary64: means, then centred sums.  out: device double[8] =

@@ -12,7 +12,7 @@ Parity status of each function (what pins it is listed in the tests):
   simulate           pinned: inverse-Gaussian law (constant model), <N> and
                      Var N from the backward equations, E[w] = 1, log w = 0 at
                      b = 0, the brute-force path likelihood ratio; power-law
-                     bias (§3.5 Eq. (26)): p = 1 equals the constant bias,
+                     bias (§3.4 Eq. (26)): p = 1 equals the constant bias,
                      path likelihood ratio for p = 0, 2.5, 3, backward-equation
                      mean with drift D + A phi^3, E[w] = 1, classical duration;
                      polynomial potential (§2.3 Eq. (17)): c2 = m^2/2 equals the
@@ -107,7 +107,7 @@ def make_run(*, model=MODEL_QUADRATIC, m=1.0, a0=0.0, s0=0.0, phi_in, phi_end=ma
              phi_uv=math.inf, dN, b=0.0, n_max, seed=0, set_id=0, traj_offset=0, mlp=None,
              mlp_norm=(0.0, 1.0, 0.0, 1.0), k_eval=1, bias_p=None, poly=None):
     """One parameter set.  b is the amplitude of B = b S(phi), or, with bias_p
-    given, of the power law B = b phi^bias_p (§3.5 Eq. (26)).  poly: the
+    given, of the power law B = b phi^bias_p (§3.4 Eq. (26)).  poly: the
     coefficients c_k of V = sum_k c_k phi^k for model=MODEL_POLYNOMIAL."""
     r = OracleRun()
     r.model, r.m, r.a0, r.s0 = model, m, a0, s0

@@ -163,7 +163,7 @@ def estimate(N, logw, n_bins, lo, hi, n_sub=1, id_offset=0):
 
 
 def pearson(N, logw):
-    """Pearson's r of (N, ln w) over the runs with finite N (§3.5), with the
+    """Pearson's r of (N, ln w) over the runs with finite N (§3.4), with the
     count, means and unbiased (co)variances; r is NaN for fewer than 2 runs or
     a zero variance."""
     N = np.asarray(N, dtype=np.float64)

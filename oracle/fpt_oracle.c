@@ -242,7 +242,7 @@ static int64_t run_one(const oracle_run* r, uint64_t traj, double* N_out, double
         blk_xisum += xi;
         const double D = drift(r, phi);
         const double S = noise(r, phi);
-        /* §2.3 Eq. (18) with f = S, or the power law of §3.5 Eq. (26) */
+        /* §2.3 Eq. (18) with f = S, or the power law of §3.4 Eq. (26) */
         const double B = r->bias_kind == ORACLE_BIAS_POWER ? r->b * pow(phi, r->bias_p) : b_cur * S;
         /* §2.2 Eq. (11): x_{m+1} - x_m = [D + B] dt + S xi sqrt(dt) */
         double phi_new = phi + (D + B) * dN + S * xi * sq;

@@ -30,7 +30,7 @@ extern "C" {
 
 /* Bias kinds (§2.3 Eq. (18): B = A f(phi)). */
 #define ORACLE_BIAS_CONST 0 /* B = b S(phi): f = S, A = b */
-#define ORACLE_BIAS_POWER 1 /* B = b phi^p (§3.5 Eq. (26)): A_p = b, p = bias_p */
+#define ORACLE_BIAS_POWER 1 /* B = b phi^p (§3.4 Eq. (26)): A_p = b, p = bias_p */
 #define ORACLE_BIAS_MLP 2   /* B = b(phi, N_elapsed) S(phi), b an MLP re-evaluated every k_eval steps */
 
 #define ORACLE_MLP_HIDDEN 64

@@ -6,7 +6,7 @@
 // errors over the histogram's n_sub subsets (§2.1); the multi-bias
 // reconstruction of §3.2 (estimates of the same bins from several bias
 // amplitudes, combined where they overlap); and Pearson's r of (N, ln w) over
-// all runs, the measure of §3.5's search for the power-law bias.
+// all runs, the measure of §3.4's search for the power-law bias.
 //
 // One thread per bin, binary64 throughout.  The thread reads the bin's n_sub
 // subset entries, each holding max-shifted sums about its own maximum, and

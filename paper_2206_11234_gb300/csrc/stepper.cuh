@@ -21,7 +21,7 @@
 // steps has ln w = -b sqrt(dN) W - b^2 M dN / 2 with W = sum xi.  W is summed
 // per block in the state precision and folded into a running sum that is
 // either compensated binary32 (Kahan) or binary64.  With the power-law bias
-// B = A_p phi^p (§3.5 Eq. (26)) the amplitude B/S changes every step, so the
+// B = A_p phi^p (§3.4 Eq. (26)) the amplitude B/S changes every step, so the
 // power models sum the step log-weights themselves instead of the normals.
 #pragma once
 #include <cstdint>
@@ -263,7 +263,7 @@ struct ModelStep<double, FPT_MODEL_POLYNOMIAL> {
     }
 };
 
-// Quadratic potential with B = A_p phi^p (§3.5 Eq. (26)), binary64: the update
+// Quadratic potential with B = A_p phi^p (§3.4 Eq. (26)), binary64: the update
 // of Eq. (11) and the step's log-weight -(B/S^2)(B dN/2 + S xi sqrt(dN)) of
 // Eqs. (12)-(14), as written.
 template <int MODEL>

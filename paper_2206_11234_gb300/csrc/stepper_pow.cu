@@ -1,5 +1,5 @@
 // Binary32-state instantiations of the persistent stepper with the power-law
-// bias B = A_p phi^p (§3.5 Eq. (26)): p in 0..4 specialised, any other real p
+// bias B = A_p phi^p (§3.4 Eq. (26)): p in 0..4 specialised, any other real p
 // through exp2/log2; one scheduling block length (32 steps).
 #include "stepper.cuh"
 #include "stepper_launch.h"

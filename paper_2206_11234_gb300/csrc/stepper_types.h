@@ -10,7 +10,7 @@ namespace fpt {
 constexpr int kStepperMaxThreads = 512;
 
 // Model tags of the quadratic potential with the power-law bias B = A_p phi^p
-// (§3.5 Eq. (26)): kModelPow + p for an integer p in 0..4 (phi^(p-1) by
+// (§3.4 Eq. (26)): kModelPow + p for an integer p in 0..4 (phi^(p-1) by
 // multiplies), kModelPowReal for any real p (phi^(p-1) = 2^((p-1) log2 phi)).
 constexpr int kModelPow = 16;
 constexpr int kModelPowReal = kModelPow + 15;

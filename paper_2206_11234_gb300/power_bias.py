@@ -1,4 +1,4 @@
-"""Host side of the power-law bias search of arXiv:2206.11234 §3.5.
+"""Host side of the power-law bias search of arXiv:2206.11234 §3.4.
 
 The bias B = A_p phi^p (Eq. (26)) is compared across p at equal displacement
 of the sample distribution: A_p is chosen so that the classical duration of

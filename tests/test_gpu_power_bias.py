@@ -1,4 +1,4 @@
-"""Power-law bias B = A_p phi^p (§3.5 Eq. (26)) on the GPU against the FP64
+"""Power-law bias B = A_p phi^p (§3.4 Eq. (26)) on the GPU against the FP64
 oracle running the same bias.
 
 * FP64 stepper, per run: the same crossing step for every run, |dN| <= 1e-12 N

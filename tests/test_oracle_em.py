@@ -234,7 +234,7 @@ def test_biased_and_direct_histograms_agree():
     assert compared >= 8
 
 
-# ---- power-law bias B = A_p phi^p (§3.5 Eq. (26)) ----
+# ---- power-law bias B = A_p phi^p (§3.4 Eq. (26)) ----
 
 C0 = 1.0 / (2.0 * math.pi * math.sqrt(6.0))
 

@@ -1,4 +1,4 @@
-"""Host helpers of the power-law bias search (§3.5): the classical duration
+"""Host helpers of the power-law bias search (§3.4): the classical duration
 against its closed form at A = 0 and against scipy quadrature, the amplitude
 tuning, and the small-noise sigma_N against the backward-equation variance."""
 import math
