@@ -30,6 +30,7 @@ Parity status of each function (what pins it is listed in the tests):
 import ctypes
 import math
 import os
+import threading
 
 import numpy as np
 
@@ -72,9 +73,16 @@ class OracleRun(ctypes.Structure):
 
 _lib = None
 _keep = []
+_lib_lock = threading.Lock()
 
 
 def lib():
+    global _lib
+    with _lib_lock:  # callers may be threads: build and load once
+        return _lib_locked()
+
+
+def _lib_locked():
     global _lib
     if _lib is None:
         path = _build.build()

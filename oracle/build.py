@@ -7,6 +7,7 @@ so that every expression in fpt_oracle.c is rounded as written on any host
 import os
 import subprocess
 import sys
+import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "fpt_oracle.c")
@@ -18,7 +19,7 @@ def build(force: bool = False) -> str:
         os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "fpt_oracle.h"))
     ):
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = LIB + f".tmp{os.getpid()}.{threading.get_ident()}"  # unique per process and thread
     cmd = [
         os.environ.get("CC", "cc"), "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
         "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wextra",
