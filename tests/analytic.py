@@ -29,6 +29,16 @@ Monte Carlo must reproduce.
   exponentials (Eqs. (A.7), (A.19)); confluent hypergeometric functions from mpmath.
 * ``edgeworth_pdf``: Appendix B, Eq. (B.10), with the probabilists' Hermite
   polynomial He_3(x) = x^3 - 3x (Eq. (B.7) prints x^2 - 1).
+* ``mgf_cumulants``, ``SaddlepointDensity``: K(s) = ln E[e^{sN}] and its first
+  four derivatives from the Riccati form of the backward equation for the
+  characteristic function of Appendix A on the real axis, and the density of N
+  by the saddle-point approximation (Daniels 1954) — the far tail where the
+  Edgeworth series of Appendix B no longer holds.  Pinned by
+  ``constant_model_log_mgf`` (Brownian motion with drift, closed form),
+  ``quad_log_mgf_appendix_a`` (the hypergeometric solution of Appendix A) and
+  the backward cumulants.
+* ``em_classical_shift``: the delay of the noise-free Euler-Maruyama map
+  against the classical duration (the leading O(dN) bias of <N>).
 """
 import math
 import warnings
@@ -349,3 +359,145 @@ def path_log_likelihood_ratio(phi, b_used, drift_fn, noise_fn, dN):
     lt = stats.norm.logpdf(dx, loc=D * dN, scale=S * math.sqrt(dN))
     ls = stats.norm.logpdf(dx, loc=(D + B) * dN, scale=S * math.sqrt(dN))
     return float(np.sum(lt - ls))
+
+
+# ---- the moment generating function of N and its saddle-point inversion ----
+
+def mgf_cumulants(s, phi_in, drift, noise, phi_end, phi_top, rtol=1e-12):
+    """(K, K', K'', K''', K'''') at real s, K(s) = ln E[exp(s N)] for runs from
+    phi_in: the characteristic function of Appendix A (Eq. (A.2)) on the real
+    axis.  M = E[e^{sN}] solves (S^2/2) M'' + D M' + s M = 0 with M(phi_end) = 1
+    and M'(phi_top) = 0 (reflecting wall); y = M'/M obeys the Riccati equation
+    y' = -y^2 - (2/S^2)(D y + s).  It is stiff when drift dominates (2|D|/S^2 is
+    huge) but stable integrated from the wall down to phi_end (Radau).  The
+    s-derivatives y_k obey the differentiated equations, and
+    K^(k)(s) = integral of y_k from phi_end to phi_in.  Finite for s below the
+    domain's leading decay rate."""
+    from scipy.integrate import solve_ivp
+
+    def rhs(phi, u):
+        y0, y1, y2, y3, y4 = u[:5]
+        S = noise(phi)
+        g = 2.0 / (S * S)
+        D = drift(phi)
+        return [-y0 * y0 - g * (D * y0 + s),
+                -2 * y0 * y1 - g * (D * y1 + 1.0),
+                -2 * y1 * y1 - 2 * y0 * y2 - g * D * y2,
+                -6 * y1 * y2 - 2 * y0 * y3 - g * D * y3,
+                -6 * y2 * y2 - 8 * y1 * y3 - 2 * y0 * y4 - g * D * y4,
+                y0, y1, y2, y3, y4]
+
+    def jac(phi, u):
+        y0, y1, y2, y3, y4 = u[:5]
+        S = noise(phi)
+        c = -2 * y0 - 2.0 * drift(phi) / (S * S)
+        J = np.zeros((10, 10))
+        J[0, 0] = c
+        J[1, 0], J[1, 1] = -2 * y1, c
+        J[2, 0], J[2, 1], J[2, 2] = -2 * y2, -4 * y1, c
+        J[3, 0], J[3, 1], J[3, 2], J[3, 3] = -2 * y3, -6 * y2, -6 * y1, c
+        J[4, 0], J[4, 1], J[4, 2], J[4, 3], J[4, 4] = -2 * y4, -8 * y3, -12 * y2, -8 * y1, c
+        J[5:, :5] = np.eye(5)
+        return J
+    sol = solve_ivp(rhs, (phi_top, phi_end), np.zeros(10), method="Radau", jac=jac, rtol=rtol, atol=1e-14,
+                    dense_output=True)
+    if not sol.success:
+        raise ArithmeticError(f"mgf_cumulants(s = {s}): {sol.message}")
+    return tuple(float(v) for v in sol.sol(phi_in)[5:] - sol.y[5:, -1])
+
+
+class SaddlepointDensity:
+    """The density of N from K(s) = ln E[e^{sN}] by the saddle-point
+    approximation with its first correction (Daniels 1954):
+        f(N) = exp(K(s) - s N) / sqrt(2 pi K''(s)) (1 + lambda_4/8 - 5 lambda_3^2/24),
+    K'(s) = N, lambda_k = K^(k)(s) / K''(s)^(k/2).  K, K', K'' and K''' are
+    tabulated on a grid of s and interpolated by cubic Hermite polynomials built
+    on the exact derivatives (K'''' linearly), so one table serves every N with
+    K'(s) inside it."""
+
+    def __init__(self, s_grid, table, mgf=None):
+        from scipy.interpolate import CubicHermiteSpline
+        self.mgf = mgf
+        self.s = np.asarray(s_grid, dtype=np.float64)
+        t = np.asarray(table, dtype=np.float64)
+        self.t = t
+        self.K = CubicHermiteSpline(self.s, t[:, 0], t[:, 1])
+        self.K1 = CubicHermiteSpline(self.s, t[:, 1], t[:, 2])
+        self.K2 = CubicHermiteSpline(self.s, t[:, 2], t[:, 3])
+        self.K3 = CubicHermiteSpline(self.s, t[:, 3], t[:, 4])
+
+    @classmethod
+    def from_mgf(cls, s_grid, mgf):
+        return cls(s_grid, [mgf(s) for s in s_grid], mgf)
+
+    def saddlepoint(self, N):
+        from scipy.optimize import brentq
+        return brentq(lambda s: float(self.K1(s)) - N, self.s[0], self.s[-1], xtol=1e-13, rtol=1e-15)
+
+    def pdf(self, N, correction=True, exact=False):
+        """exact=True refines each saddle point by Newton steps on the
+        generating function itself and takes K and its derivatives from it
+        (a few solves per N) instead of the table."""
+        out = []
+        for x in np.atleast_1d(np.asarray(N, dtype=np.float64)):
+            s = self.saddlepoint(x)
+            if exact:
+                for _ in range(8):  # Newton on K'(s) = N with the exact derivatives
+                    k0, k1, k2, k3, k4 = self.mgf(s)
+                    if abs(k1 - x) <= 1e-13 * abs(x):
+                        break
+                    s -= (k1 - x) / k2
+            else:
+                k0, k2, k3 = float(self.K(s)), float(self.K2(s)), float(self.K3(s))
+                k4 = float(np.interp(s, self.s, self.t[:, 4]))
+            f = math.exp(k0 - s * x) / math.sqrt(2 * math.pi * k2)
+            if correction:
+                l3, l4 = k3 / k2 ** 1.5, k4 / k2 ** 2
+                f *= 1 + l4 / 8 - 5 * l3 * l3 / 24
+            out.append(f)
+        return np.array(out)
+
+    def bin_average(self, lo, hi, nodes=6):
+        """(1/(hi - lo)) integral of the density over (lo, hi], Gauss-Legendre."""
+        x, w = np.polynomial.legendre.leggauss(nodes)
+        return 0.5 * float(np.sum(w * self.pdf(0.5 * (hi - lo) * x + 0.5 * (hi + lo))))
+
+
+def constant_model_log_mgf(s, distance, speed, sigma):
+    """ln E[e^{sN}] for Brownian motion with drift `speed` > 0 toward a barrier at
+    `distance` and volatility sigma: (distance/sigma^2)(speed - sqrt(speed^2 - 2 sigma^2 s))."""
+    return distance / sigma**2 * (speed - math.sqrt(speed * speed - 2 * sigma * sigma * s))
+
+
+def quad_log_mgf_appendix_a(s, m, phi, phi_end, phi_uv, dps=30):
+    """ln E[e^{sN}] for quadratic inflation with a reflecting wall from the
+    closed form of Appendix A: chi = (f g'_uv - g f'_uv) / (f_end g'_uv - g_end f'_uv)
+    with f, g of Eq. (A.11) at alpha = sqrt(1 - 4 s / v0) (imaginary above
+    s = v0/4, where f and g are complex conjugates and chi is real)."""
+    mp = _mp()
+    mp.mp.dps = dps
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+    al = mp.sqrt(mp.mpc(1 - 4 * mp.mpf(s) / v0))
+    f, _ = _quad_f(mp, m, al, phi)
+    g, _ = _quad_f(mp, m, -al, phi)
+    fe, _ = _quad_f(mp, m, al, phi_end)
+    ge, _ = _quad_f(mp, m, -al, phi_end)
+    _, fu = _quad_f(mp, m, al, phi_uv)
+    _, gu = _quad_f(mp, m, -al, phi_uv)
+    chi = (f * gu - g * fu) / (fe * gu - ge * fu)
+    return float(mp.log(mp.re(chi)))
+
+
+def em_classical_shift(phi_in, dN, phi_end=math.sqrt(2.0)):
+    """How much later the noise-free Euler-Maruyama map of quadratic inflation,
+    phi <- phi - 2 dN / phi (§2.2 Eq. (11) without noise and bias), crosses
+    phi_end than the classical N_cl = (phi_in^2 - phi_end^2)/4, with the
+    crossing interpolated linearly within the last step.  To first order in dN
+    it is dN/2 ln(phi_in/phi_end): the leading discretisation error of <N> in
+    drift domination."""
+    phi, k = phi_in, 0
+    while True:
+        nxt = phi - 2.0 * dN / phi
+        if nxt <= phi_end:
+            return (k + (phi - phi_end) / (phi - nxt)) * dN - (phi_in ** 2 - phi_end ** 2) / 4.0
+        phi, k = nxt, k + 1
