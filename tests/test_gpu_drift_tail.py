@@ -155,7 +155,9 @@ def test_fig9_paper_workload(nat):
     dN), binary64 path, 100 bins of sigma_N / 4 from -6 to +19 sigma.  <N> is
     K'(0) plus the Euler-Maruyama delay; the lognormal estimates of A <= 2
     (variance of ln w in a bin <= 9) agree with the saddle point within 4
-    errors + 1 %; A = 3 and 4 are printed (the lognormal estimator's bias
+    errors + 1 %.  At A = 3 (the paper's Fig. 1) the naive estimates fall well
+    below P (the sampling problem of §2.4) while the lognormal ones lie within
+    0.1 in ln P.  A = 3 and 4 are printed (the lognormal estimator's bias
     grows with that variance: +4 % and +7 % there, P ~ 1e-41), with the
     Gaussian approximation the paper draws, which the skewness of N puts 0.6
     below the saddle point in ln P at 11 sigma and 1.1 below at 14 sigma."""
@@ -204,6 +206,14 @@ def test_fig9_paper_workload(nat):
               f"mean ln(p/P) {np.sum(w * dev) / np.sum(w):+.4f}, max |dev|/err {np.max(np.abs(dev) / err):.2f}, "
               f"median var ln w {np.median(e['var_lw'][use]):.3g}; ln(Gaussian/P) at the deepest bin "
               f"{math.log(gauss[use][-1] / P[use][-1]):+.3f}")
+        devd = np.log(np.maximum(e["p_direct"][use], 1e-300) / P[use])
+        wd = e["count"][use]
+        print(f"      direct (Eq. (16)) count-weighted mean ln(p/P) {np.sum(wd * devd) / np.sum(wd):+.3f}")
         assert use.sum() >= 15
         if a <= 2.0:
             assert np.all(np.abs(dev) <= 4 * err + 0.01), (a, np.max(np.abs(dev) / (4 * err + 0.01)))
+        if a == 3.0:
+            # Fig. 1 (same m, phi_in and A): the naive estimate misses the rare
+            # large weights and falls well below P, the lognormal one does not
+            assert np.sum(wd * devd) / np.sum(wd) < -0.5
+            assert abs(np.sum(w * dev) / np.sum(w)) < 0.1
