@@ -22,8 +22,11 @@ density is taken at N minus that delay.
   discretisation error left after the delay (+0.55 % at dN = 1e-3, +0.33 % at
   5e-4 in the mean over the tail bins).
 
-* The paper's own drift-dominated workload (§3.3 Fig. 9, m = 0.001, wall at
-  phi_in = sqrt(42), binary64): <N> and the lognormal estimates of A <= 2.
+* The paper's own drift-dominated workloads, binary64: §3.3 Fig. 9 (m = 0.001,
+  wall at phi_in = sqrt(42)): <N> and the lognormal estimates of A <= 2, and
+  at A = 3 (Fig. 1) the naive estimator's shortfall; §3.4 Fig. 10 (p = 3
+  against p = 1 at 4e4 runs): the p = 3 naive estimates and their smaller
+  errors.
 
 Also printed, not asserted: the lognormal estimates of the b = 2 and b = 4
 sets.  At b = 4 ln w has variance ~31 within a bin; there the estimate lies
@@ -217,3 +220,64 @@ def test_fig9_paper_workload(nat):
             # large weights and falls well below P, the lognormal one does not
             assert np.sum(wd * devd) / np.sum(wd) < -0.5
             assert abs(np.sum(w * dev) / np.sum(w)) < 0.1
+
+
+def test_fig10_power_law_against_constant_bias(nat):
+    """§3.4 Fig. 10: m = 0.001, phi_in = 6 (the paper does not give it), no
+    wall, A_p placing the classical sample duration 8 sigma past the target's,
+    4e4 runs per p (the paper's count), dN = sigma_N / 20, binary64 path.  The
+    naive estimates of the p = 3 set agree with the saddle point within 4
+    standard errors + 1 % in every bin with >= 400 runs, with smaller errors
+    than the lognormal estimates of the p = 1 set in the same bins (printed
+    against the reference too)."""
+    import torch
+    m, phi_in = 1e-3, 6.0
+    D = lambda x: A.quad_drift(x, 0.0, m)
+    S = lambda x: A.quad_noise(x, m)
+    mgf = lambda s: A.mgf_cumulants(s, phi_in, D, S, SQ2, 7.0)
+    k = mgf(0.0)
+    sig = math.sqrt(k[2])
+    dN = sig / 20
+    sp = A.SaddlepointDensity.from_mgf(np.arange(1000.0, 8001.0, 200.0), mgf)
+    delay = A.em_classical_shift(phi_in, dN)
+    nb, lo, hi = 64, k[1] + 2 * sig, k[1] + 18 * sig
+    edges = lo + (hi - lo) / nb * np.arange(nb + 1)
+    P = np.array([sp.bin_average(edges[j] - delay, edges[j + 1] - delay)
+                  if sp.K1(sp.s[0]) < edges[j] - delay and edges[j + 1] - delay < sp.K1(sp.s[-1]) else np.nan
+                  for j in range(nb)])
+    sig_cl = PB.classical_sigma(m, phi_in)
+    target = PB.classical_duration(0.0, 1.0, phi_in) + 8 * sig_cl
+    n = 40000
+    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    lw = torch.empty(n, dtype=torch.float64, device="cuda")
+    res = {}
+    for p in (1.0, 3.0):
+        amp = PB.tune_amplitude(p, target, phi_in)
+        prm = nat.make_params(precision="f64", m=m, n_max=hi, bias_p=p)
+        nat.fpt_simulate(prm, n, phi_in, SQ2, math.inf, dN, amp, 0, N, lw)
+        r = nat.fpt_pearson(N, lw)
+        bins = nat.empty_bins(nb * N_SUB)
+        counts = nat.empty_counts(1)
+        nat.fpt_histogram(N, lw, nb, lo, hi, bins, counts, n_sub=N_SUB)
+        est = nat.empty_estimates(nb)
+        nat.fpt_estimate(bins, nb, lo, hi, n, est, n_sub=N_SUB)
+        torch.cuda.synchronize()
+        res[p] = (nat.estimates_to_dict(est), abs(r["r"]))
+    e1, r1 = res[1.0]
+    e3, r3 = res[3.0]
+    use = (e3["count"] >= 400) & (e1["count"] >= 400) & np.isfinite(P)
+    d3 = np.log(e3["p_direct"][use] / P[use])
+    s3 = e3["se_direct"][use] / e3["p_direct"][use]
+    d1 = np.log(e1["p_lognormal"][use] / P[use])
+    s1 = np.hypot(0.5 * (e1["eps_lo"][use] + e1["eps_hi"][use]) / e1["p_lognormal"][use],
+                  1 / np.sqrt(e1["count"][use]))
+    z = (0.5 * (edges[1:] + edges[:-1]) - k[1]) / sig
+    print(f"|r| p = 1: {r1:.4f}, p = 3: {r3:.6f}; {use.sum()} common bins, z {z[use].min():.1f}..{z[use].max():.1f}, "
+          f"P down to {P[use].min():.1e}")
+    print(f"p = 3 naive: max |dev|/se {np.max(np.abs(d3) / s3):.2f}, median relative error {np.median(s3):.4f}; "
+          f"p = 1 lognormal: mean dev {np.mean(d1):+.4f}, max |dev|/err {np.max(np.abs(d1) / s1):.2f}, "
+          f"median relative error {np.median(s1):.4f}")
+    assert r3 > 0.9999 > r1
+    assert use.sum() >= 8
+    assert np.all(np.abs(d3) <= 4 * s3 + 0.01), np.max(np.abs(d3) / (4 * s3 + 0.01))
+    assert np.median(s3) < np.median(s1)
