@@ -36,6 +36,10 @@ ALG_INST_PER_STEP = 38 / 4 + 15 / 2 + 7
 MUFU_PER_STEP = 3.0  # lg2 + sqrt + sin + cos per 2 steps, rcp per step
 ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 schedulers)
 MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock
+# learned bias: per run and evaluation, 2 x 64 tanh on the XU pipe and
+# 2*64 + 64*64 + 64 multiply-adds (2 -> 64 -> 64 -> 1) on the tensor cores
+MLP_TANH_PER_EVAL = 128
+MLP_MAC_PER_EVAL = 2 * 64 + 64 * 64 + 64
 
 
 # Sources the binary32 stepper kernel is built from: DRAM counters recorded
@@ -289,6 +293,25 @@ def run_learned_bias(args):
                "train_seconds": train_s, "train_runs": n_t * args.train_steps,
                "rel_second_moment_log_first": hist[0]["log_second_moment"] - 2 * math.log(max(hist[0]["p_hat"], 1e-300)),
                "rel_second_moment_log_last": hist[-1]["log_second_moment"] - 2 * math.log(max(hist[-1]["p_hat"], 1e-300))}
+    # roofline of the learned-bias stepper: the XU (MUFU) pipe binds, with the
+    # constant-bias step's 3 operations per step plus 128 tanh per run every
+    # k_eval steps; the tensor-core term is reported beside it
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    mufu_per_step = MUFU_PER_STEP + MLP_TANH_PER_EVAL / args.k_eval
+    mufu_rate = learned["steps_per_s"] / 32 * mufu_per_step
+    mufu_peak = n_sm * MUFU_PER_SM_CLK * f_max
+    tflops = learned["steps_per_s"] * 2 * MLP_MAC_PER_EVAL / args.k_eval / 1e12
+    bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    roofline = {"bound": "alu", "achieved": mufu_rate / 1e9, "peak": mufu_peak / 1e9,
+                "unit": "Gwarp-MUFU/s (algorithmic, XU pipe)", "frac": mufu_rate / mufu_peak, "traffic": None,
+                "kernel": f"stepper_mlp_kernel<{args.k_eval}>",
+                "mufu_per_warp_step": mufu_per_step,
+                "peak_source": f"{n_sm} SMs x 16 MUFU lanes/clk x {f_max / 1e6:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+                "tensor_term": {"achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s (bf16)",
+                                "frac": tflops / bf16_peak if bf16_peak else None,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS)"}}
     # FP64 oracle with the same (BF16) network on a bounded sample, all host cores
     p64 = nat.mlp_unpack_bf16(tr.master.cpu()).numpy()
     n_o = 1024
@@ -319,7 +342,7 @@ def run_learned_bias(args):
             "tail": {"event": f"N > {tail}", "reference_P_survival_pde": 1.0986e-3,
                      "best_constant": best, "learned": learned, "learned_se": se_gpu, "oracle_learned": orc,
                      "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None},
-            "ladder": ladder}
+            "roofline": roofline, "ladder": ladder}
     print(json.dumps(line))
 
 
