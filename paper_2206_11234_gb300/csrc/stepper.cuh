@@ -497,14 +497,18 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-// Register cap per thread.  56 leaves every binary32 instantiation spill-free
-// (48 spilled a few words in the Kahan and power-law variants) at 32 resident
-// warps per SM; measured on the drift-dominated ladder, 40 / 48 / 56 gave
-// 1.113 / 1.116 / 1.131 e12 steps/s whatever the block size, so occupancy is
-// not what bounds the loop.  The binary64 reference kernels are built with a
-// larger cap.
+// Register cap per thread.  64 is the largest that keeps 32 warps resident per
+// SM (4 blocks of 256 or 2 of 512 threads: 65,536 registers), and its spare
+// registers let the compiler overlap a block's Philox words with the previous
+// block's Box-Muller and updates.  Measured on the drift-dominated ladder
+// (steps/s of the kernel, 256 / 512 threads): 56: 1.137 / 1.140e12,
+// 64: 1.152 / 1.155e12, 72: 1.145 / 1.116e12 (fewer resident warps); 40 and
+// 48 (more warps) were no faster than 56.  At 64 the quadratic, constant and
+// power-law kernels are spill-free; the polynomial-potential ones (eight
+// coefficients per set) spill 12-48 bytes (56-84 at a cap of 56).  The binary64
+// reference kernels are built with a larger cap.
 #ifndef FPT_STEPPER_MAXNREG
-#define FPT_STEPPER_MAXNREG 56
+#define FPT_STEPPER_MAXNREG 64
 #endif
 template <typename Real, int PREC, int MODEL, bool WALL, int KS>
 __global__ void __maxnreg__(FPT_STEPPER_MAXNREG)
