@@ -257,6 +257,12 @@ def run_learned_bias(args):
         return {"b": b, "runs": n, "P": ne["P"], "n_eff": ne["n_eff"], "seconds": t, "steps": st,
                 "steps_per_s": st / t, "n_eff_per_s": ne["n_eff"] / t, "n_eff_per_Msteps": 1e6 * ne["n_eff"] / st}
 
+    # the constant-bias runs take the library's autotuned launch shape (cached for
+    # this precision, model and wall), as the main benchmark does
+    pilot = W.SetSpec(n_traj=max(4096, int((1 << 22) * args.scale)), b=0.4, hist_lo=0.0, hist_hi=60.0, n_bins=512,
+                      **base)
+    tuned = nat.fpt_autotune(nat.make_params(precision="f32_f64acc", m=1.0, n_max=60.0, stream=stream),
+                             nat.make_sets([pilot]), seed=99, fraction=0.02)
     n_c = max(4096, int((1 << 20) * args.scale))
     ladder = [constant(b, n_c, 11) for b in (0.0, 0.2, 0.4, 0.6, 0.8, 1.0, 2.0, 4.0, 6.0)]
     best_b = max(ladder, key=lambda r: r["n_eff_per_Msteps"])["b"]
@@ -338,7 +344,8 @@ def run_learned_bias(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "learned bias vs constant: m=1 phi_in=8 phi_uv=9 dN=5e-4, tail N > 40",
                        "scale": args.scale, "train_steps": args.train_steps, "lr": args.lr,
-                       "k_eval": args.k_eval},
+                       "k_eval": args.k_eval,
+                       "constant_launch_shape": {"block_dim": tuned[0], "k_steps": tuned[1]}},
             "tail": {"event": f"N > {tail}", "reference_P_survival_pde": 1.0986e-3,
                      "best_constant": best, "learned": learned, "learned_se": se_gpu, "oracle_learned": orc,
                      "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None},
