@@ -14,11 +14,14 @@ state with binary64 log-weight sums, dN = 5e-4 (the paper gives no dN).
   the paper calls next-to-leading: the paper's leading pole v0/4 is not a
   root when the wall is this close).  With 2^24 runs per amplitude the same
   holds with errors 20 times smaller.
-* Fig. 4 (A = 0.4, walls at phi_in x 1, 1.2, 1.4, 2^22 runs each): each wall's
-  histogram follows its own pole expansion; near the peak the walls at 1.2 and
-  1.4 phi_in give the same density, and they separate only in the tail (from
-  N ~ 20 on), which decays at each wall's leading root (0.6528, 0.3798,
-  0.2458).
+* Fig. 4 (A = 0.4, walls at phi_in x 1, 1.2, 1.4 and none, 2^22 runs each):
+  each wall's histogram follows its own pole expansion; near the peak the walls
+  at 1.2 and 1.4 phi_in give the same density, and they separate only in the
+  tail (from N ~ 20 on), which decays at each wall's leading root (0.6528,
+  0.3798, 0.2458).  Without a wall (the paper's phi_uv -> infinity limit, whose
+  branch-cut integral of Eq. (A.28) is not used here) the histogram follows
+  the survival PDE with a far wall, and near the peak equals the 1.4 phi_in
+  wall's.
 """
 import math
 
@@ -31,6 +34,7 @@ from paper_2206_11234_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 pytest.importorskip("mpmath")
 R42 = math.sqrt(42.0)
+SQ2 = math.sqrt(2.0)
 DN = 5e-4
 LO, HI, NB, N_SUB = 0.0, 80.0, 160, 20
 WIDTH = (HI - LO) / NB
@@ -120,15 +124,36 @@ def test_fig3_wall_at_the_start(nat):
     assert reach[0][0] < 1e-2 and reach[0][1] < 1e-4 and reach[0][2] < 1e-9, reach[0]
 
 
+def _no_wall_bins():
+    """The phi_uv -> infinity limit: bin averages of the survival PDE with the
+    wall at 20, where it no longer matters (a wall at 30 changes them by < 1e-5
+    out to N = 30)."""
+    D = lambda x: A.quad_drift(x, 0.0, 1.0)
+    S = lambda x: A.quad_noise(x, 1.0)
+    Q = A.survival_pde(R42, D, S, SQ2, 20.0, EDGES, n=6001, dN=2e-3)
+    P = (Q[:-1] - Q[1:]) / WIDTH
+    P[EDGES[:-1] < N_FROM] = np.nan
+    return P
+
+
 def test_fig4_wall_position(nat):
-    walls = (R42, 1.2 * R42, 1.4 * R42)
-    ref = [_pole_bins(u) for u in walls]
-    es = _simulate(nat, (0.4,) * 3, walls, 1 << 22, 5)
+    walls = (R42, 1.2 * R42, 1.4 * R42, math.inf)
+    ref = [_pole_bins(u) for u in walls[:3]]
+    es = _simulate(nat, (0.4,) * 4, walls, 1 << 22, 5)
     for (P, lam0), e, u in zip(ref, es, walls):
         _compare(e, P, f"wall {u / R42:.1f} phi_in")
         rate, span = _fit_rate([e], P, 25.0 if u > R42 else 15.0)
         print(f"wall {u / R42:.1f} phi_in: tail rate {rate:.4f}, leading root {lam0:.4f}")
         assert abs(rate / lam0 - 1) < 0.03, (u, rate, lam0)
+    # no wall (the paper's phi_uv -> infinity curve): the far-wall survival PDE,
+    # and near the peak the same density as the wall at 1.4 phi_in
+    P_inf = _no_wall_bins()
+    _compare(es[3], P_inf, "no wall")
+    pk = (EDGES[:-1] >= 6.0) & (EDGES[1:] <= 8.0)
+    d = np.abs(np.log(es[3]["p_direct"][pk] / es[2]["p_direct"][pk]))
+    sg = np.hypot(es[3]["se_direct"][pk] / es[3]["p_direct"][pk], es[2]["se_direct"][pk] / es[2]["p_direct"][pk])
+    assert np.all(d <= 4 * sg + 0.01), np.max(d / sg)
+    es = es[:3]
     # near the peak (N <= 8) the walls at 1.2 and 1.4 phi_in are indistinguishable
     # (their expansions agree to 5e-5); from N ~ 20 on they separate (expansions:
     # 5 % at N = 20, 2.4 times at N = 30, 4.5 times at N = 35)
