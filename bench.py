@@ -756,7 +756,10 @@ def main():
     n_sm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     issue_peak = n_sm * ISSUE_PER_SM_CLK * f_max  # warp-instructions/s
-    steps_peak = min(issue_peak / ALG_INST_PER_STEP, n_sm * MUFU_PER_SM_CLK * f_max / MUFU_PER_STEP) * 32
+    mufu_peak = n_sm * MUFU_PER_SM_CLK * f_max  # warp-MUFU operations/s
+    issue_steps_peak = issue_peak / ALG_INST_PER_STEP * 32
+    mufu_steps_peak = mufu_peak / MUFU_PER_STEP * 32
+    steps_peak = min(issue_steps_peak, mufu_steps_peak)
     achieved_steps = stepper_steps / (ms_stepper / 1e3)
     shape = tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}
     ctr = stepper_counters(wl.precision, shape.get("block_dim"), shape.get("k_steps"))
@@ -769,16 +772,25 @@ def main():
                     "branch_targets_uniform_pct": ctr["branch_targets_uniform_pct"],
                     "active_lanes_per_inst_pct": 100.0 * ctr["thread_inst_executed"] / (32.0 * ctr["inst_executed"]),
                     "source": "profiles/stepper_counters.json"}
-    roof = {"bound": "alu", "achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9,
-            "peak": issue_peak / 1e9, "unit": "Gwarp-inst/s (algorithmic)",
-            "frac": achieved_steps / steps_peak,
+    # reported against the binding one of the two co-bounds (issue slots, XU pipe)
+    if mufu_steps_peak <= issue_steps_peak:
+        a_, p_, u_ = achieved_steps * MUFU_PER_STEP / 32 / 1e9, mufu_peak / 1e9, "Gwarp-MUFU/s (algorithmic, XU pipe)"
+    else:
+        a_, p_, u_ = achieved_steps * ALG_INST_PER_STEP / 32 / 1e9, issue_peak / 1e9, "Gwarp-inst/s (algorithmic)"
+    roof = {"bound": "alu", "achieved": a_, "peak": p_, "unit": u_, "frac": a_ / p_,
+            "issue_term": {"achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9, "peak": issue_peak / 1e9,
+                           "unit": "Gwarp-inst/s", "frac": achieved_steps / issue_steps_peak,
+                           "inst_per_warp_step": ALG_INST_PER_STEP},
+            "xu_term": {"achieved": achieved_steps * MUFU_PER_STEP / 32 / 1e9, "peak": mufu_peak / 1e9,
+                        "unit": "Gwarp-MUFU/s", "frac": achieved_steps / mufu_steps_peak,
+                        "mufu_per_warp_step": MUFU_PER_STEP},
             "traffic": (ctr["dram_read_bytes"] + ctr["dram_write_bytes"]) * n / ctr["runs"] if ctr else None,
             "vs_measured_instructions": measured,
             "kernel": f"stepper_kernel<float, {wl.precision}, quadratic, "
                       f"k_steps {(tuned or {}).get('k_steps', args.k_steps)}>",
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
-            "peak_source": f"{n_sm} SMs x 4 issue/clk x {f_max / 1e6:.0f} MHz (max SM clock, "
-                           "MEASURED_PEAKS.json); MUFU co-bound 16/clk/SM"}
+            "peak_source": f"{n_sm} SMs x 4 issue/clk and x 16 MUFU lanes/clk, x {f_max / 1e6:.0f} MHz "
+                           "(max SM clock, MEASURED_PEAKS.json)"}
     if wl.precision == "f64":
         # the binary64 reference path (per-run parity configuration): no FP64 peak
         # is measured on this machine and the FP32 issue roofline does not apply
