@@ -124,10 +124,11 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
     my_steps += (unsigned long long)M;
 }
 
-// 8 resident CTAs per SM (TMEM allows 8 x 64 columns): the bound caps the
-// kernel at 64 registers (16 bytes spilled) against 72 unbounded, which fit
-// only 7; measured on the learned-bias workload, 6.93e11 against 6.80e11
-// steps/s.
+// The bound caps the kernel at 64 registers (63 used, 16 bytes spilled; 72
+// without it).  Residency stays at 5 CTAs per SM, set by the 44 KB of shared
+// memory each holds (operand tiles and replay queues), but the schedule the
+// compiler finds under the cap waits less on dependencies: 6.93e11 against
+// 6.80e11 steps/s on the learned-bias workload.
 template <int KS>
 __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams P, const fpt_mlp_params* __restrict__ W,
                                                           const RecordSink sink) {
