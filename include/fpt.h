@@ -357,7 +357,9 @@ void fpt_autotune_reset(void);
 /* End-to-end call with HOST buffers: copies nothing in but the parameters,
  * runs fpt_simulate_batch with bins on a private device workspace and copies
  * (N, ln w) and the histograms back to host_N/host_logw (may be NULL to skip)
- * and host_bins/host_counts.  Device memory is allocated and freed inside. */
+ * and host_bins/host_counts.  The device buffers are taken from and returned
+ * to a library-owned stream-ordered pool (one per device), which keeps the
+ * memory for later calls until the process exits. */
 int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                             double* host_N, double* host_logw, fpt_bin* host_bins,
                             fpt_hist_counts* host_counts);

@@ -462,6 +462,43 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
     return rc;
 }
 
+namespace {
+// Stream-ordered memory pool of the host-buffer entry, one per device, created
+// on first use.  Its release threshold is the maximum, so the device buffers
+// one call frees stay mapped for the next; the default pool returns them to
+// the system at every synchronisation, and mapping hundreds of megabytes
+// again costs milliseconds per call.
+cudaError_t host_entry_pool(cudaMemPool_t* out) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                             double* host_N, double* host_logw, fpt_bin* host_bins,
                             fpt_hist_counts* host_counts) {
@@ -480,7 +517,10 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
     const size_t o_bins = o_lw + (rec_bytes + 255) / 256 * 256;
     const size_t o_cnt = o_bins + (bin_bytes + 255) / 256 * 256;
     const size_t total = o_cnt + cnt_bytes;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), total, st);
+    cudaMemPool_t pool;
+    cudaError_t e = host_entry_pool(&pool);
+    if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dev), total, pool, st);
     if (e != cudaSuccess) return cuda_fail(e, "device buffers");
     double* dN_ = reinterpret_cast<double*>(dev + o_N);
     double* dlw = reinterpret_cast<double*>(dev + o_lw);
