@@ -69,6 +69,23 @@ def test_histogram_concentrated_and_edge_cases(nat):
     assert np.all(c == 0) and np.all(f[:, 0] == -np.inf) and counts.cpu().tolist() == [[0, 0, 0, 0]]
 
 
+@pytest.mark.parametrize("lo,hi,n_bins", [(7.0, 10.0, 400), (0.1, 0.7, 3), (-1.3, 2.9, 4095)])
+def test_histogram_bin_edges_exact(nat, lo, hi, n_bins):
+    """Records on the bin edges lo + k d of a non-dyadic width, and one and two
+    ulp either side of them, land in the same bins as the oracle's division
+    (the kernel multiplies by 1/d and divides only next to an edge)."""
+    d = (hi - lo) / n_bins
+    k = np.arange(n_bins + 1, dtype=np.float64)
+    edges = np.concatenate([lo + k * d, k * d + lo, lo + (k + 0.5) * d, hi - (n_bins - k) * d])
+    N = np.concatenate([edges, np.nextafter(edges, np.inf), np.nextafter(edges, -np.inf),
+                        np.nextafter(np.nextafter(edges, np.inf), np.inf),
+                        np.nextafter(np.nextafter(edges, -np.inf), -np.inf)])
+    lw = np.random.default_rng(n_bins).normal(-3.0, 2.0, N.size)
+    f, c, cnt = _gpu_hist(nat, N, lw, n_bins, lo, hi)
+    rb, rc = oracle.histogram(N, lw, n_bins, lo, hi)
+    _compare(f, c, cnt, rb, rc)
+
+
 def test_histogram_rejects_bad_arguments(nat):
     import torch
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
