@@ -23,6 +23,10 @@ stepper over all sets plus the per-set histograms, seed 0.
   sum of same-signed terms in any order, (n - 1) u, plus a few ulp per term.
 * Properties at any size: ln w = 0 exactly for unbiased sets; <N> of the
   unbiased drift-dominated set against Eq. (19) to 1e-3; E[w] = 1.
+* The drift-dominated ladder in binary32 against the binary64 GPU path on the
+  same runs, every bin (the reduced-precision bar: within 3 combined sigma).
+* The learned-bias inference (2^26 runs) against the survival PDE and, on
+  sampled runs, the oracle running the same network.
 """
 import math
 from concurrent.futures import ThreadPoolExecutor
