@@ -397,6 +397,17 @@ int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* sets, int32_t
 int fpt_normals(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k0, int64_t n_blocks,
                 int32_t precision, void* out, void* stream);
 
+/* Self-test of the bounded waits (no paper counterpart).  The tensor-core
+ * kernels wait for their matrix operations on an mbarrier; each wait gives up
+ * after 2^18 attempts (about 1 s on GB300), records the expiry in a status
+ * word and lets the kernel finish, and the call then fails with
+ * FPT_EDEVICE_STATUS instead of hanging the GPU.  This entry runs that same
+ * wait, in one warp, on an mbarrier that nothing arrives at, so it must
+ * expire.  It writes *expired_out = 1 when it did, 0 otherwise, and the
+ * kernel's duration in seconds to *seconds_out (may be NULL).  The context
+ * stays usable.  Synchronises `stream`. */
+int fpt_wait_selftest(int32_t* expired_out, double* seconds_out, void* stream);
+
 /* Human-readable name of a return code (static string). */
 const char* fpt_strerror(int code);
 /* Description of the last failure in the calling thread ("" if none). */

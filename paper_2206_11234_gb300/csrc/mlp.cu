@@ -49,7 +49,10 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const fpt_mlp_params* 
     }
     __syncthreads();
     if (threadIdx.x == 0 && S.status) atomicOr(status, S.status);
-    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(S.tmem, kFwdTmemCols);
+    if ((threadIdx.x >> 5) == 0) {
+        if (S.status) tc::mbar_wait(&S.mbar, phase ^ 1u);  // a commit left pending by an expired wait
+        tc::tmem_dealloc(S.tmem, kFwdTmemCols);
+    }
 }
 
 struct MlpBwdSmem {
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) mlp_issue_z2(S);
-        if (!tc::mbar_wait(&S.mbar, phase)) S.status = 1u;
+        if (S.status != 0u || !tc::mbar_wait(&S.mbar, phase)) S.status = 1u;  // one expiry, not one per tile
         phase ^= 1u;
         tc::fence_after_sync();
         // output layer and delta2
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
                              (done > 0 || kk > 0) ? 1u : 0u);
             tc::mma_commit(&S.mbar);
         }
-        if (!tc::mbar_wait(&S.mbar, phase)) S.status = 1u;
+        if (S.status != 0u || !tc::mbar_wait(&S.mbar, phase)) S.status = 1u;  // one expiry, not one per tile
         phase ^= 1u;
         tc::fence_after_sync();
         // delta1 and the first-layer gradients
@@ -227,7 +230,10 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && S.status) atomicOr(status, S.status);
-    if (warp == 0) tc::tmem_dealloc(S.tmem, kBwdTmemCols);
+    if (warp == 0) {
+        if (S.status) tc::mbar_wait(&S.mbar, phase ^ 1u);  // a commit left pending by an expired wait
+        tc::tmem_dealloc(S.tmem, kBwdTmemCols);
+    }
 }
 
 // Grid for a persistent MLP kernel and a check that its resident CTAs cannot
@@ -268,6 +274,51 @@ size_t mlp_fwd_smem_bytes() {
 }  // namespace fpt
 
 using namespace fpt;
+
+namespace fpt {
+namespace {
+// One warp waits, with the library's bounded wait, on an mbarrier that nobody
+// arrives at; it records the expiry and then completes the phase itself, so the
+// barrier ends in a clean state.
+__global__ void wait_selftest_kernel(unsigned* __restrict__ expired) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+    __syncthreads();
+    const bool ok = tc::mbar_wait(&mbar, 0u);
+    if (!ok) atomicOr(expired, 1u);
+    __syncwarp();
+    if (threadIdx.x == 0) tc::mbar_arrive(&mbar);
+}
+}  // namespace
+}  // namespace fpt
+
+extern "C" int fpt_wait_selftest(int32_t* expired_out, double* seconds_out, void* stream) {
+    if (!expired_out) return fail(FPT_EINVAL, "expired_out is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned* d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test flag");
+    cudaMemsetAsync(d, 0, sizeof(unsigned), st);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    wait_selftest_kernel<<<1, 32, 0, st>>>(d);
+    e = cudaGetLastError();
+    cudaEventRecord(b, st);
+    unsigned h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    *expired_out = (int32_t)h;
+    if (seconds_out) *seconds_out = ms / 1e3;
+    return FPT_OK;
+}
 
 extern "C" int fpt_mlp_forward(const fpt_mlp_params* w, const float* phi, const float* N, int64_t n, float* out_b,
                                void* stream) {

@@ -181,7 +181,7 @@ __device__ __forceinline__ void mlp_tile_mma(MlpTile& S, uint32_t& phase, Issue 
         issue();
         tc::mma_commit(&S.mbar);
     }
-    if (!tc::mbar_wait(&S.mbar, phase)) S.status = 1u;
+    if (S.status != 0u || !tc::mbar_wait(&S.mbar, phase)) S.status = 1u;  // one expiry, not one per tile
     phase ^= 1u;
     tc::fence_after_sync();
 }

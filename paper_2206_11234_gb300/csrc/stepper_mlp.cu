@@ -305,7 +305,12 @@ __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams
     }
     __syncthreads();
     if (tid == 0 && F.status) atomicOr(&P.scratch->status, F.status);
-    if (warp == 0) tc::tmem_dealloc(F.tmem, kMlpTmemCols);
+    if (warp == 0) {
+        // after an expired wait the last commit may still be pending: wait for
+        // it once more (bounded) before the columns are released
+        if (F.status) tc::mbar_wait(&F.mbar, phase ^ 1u);
+        tc::tmem_dealloc(F.tmem, kMlpTmemCols);
+    }
 }
 
 size_t stepper_mlp_smem(int n_sets) {

@@ -74,6 +74,10 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(smem_u32(mbar))
+                 : "memory");
+}
 __device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -85,9 +89,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
         : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
     return ok != 0u;
 }
-// Bounded wait for the phase with the given parity; false if it did not complete.
+// Bounded wait for the phase with the given parity; false if it did not
+// complete.  A failed try_wait suspends the thread for a hardware-chosen time
+// (on GB300 1.3 us for the first few hundred attempts, ~3.7 us on average over
+// a long wait), so 2^18 attempts give up after about a second; a completing
+// tensor-core commit needs a handful.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i)
+    for (uint32_t i = 0; i < (1u << 18); ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
 }

@@ -148,6 +148,8 @@ def _load():
     L.fpt_mlp_train_step.argtypes = [P(FptParams), P(FptSet), u64, d, d, P(FptMlpTrainState),
                                      P(FptMlpTrainStats)]
     L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+    L.fpt_wait_selftest.argtypes = [P(i32), P(d), vp]
+    L.fpt_wait_selftest.restype = ctypes.c_int
     L.fpt_autotune_reset.argtypes = []
     L.fpt_autotune_reset.restype = None
     L.fpt_strerror.restype = ctypes.c_char_p
@@ -456,6 +458,15 @@ def fpt_autotune(params: FptParams, sets: ctypes.Array, seed: int = 0, fraction:
 
 def fpt_autotune_reset():
     lib.fpt_autotune_reset()
+
+
+def fpt_wait_selftest(stream=None):
+    """(expired, seconds) of the library's bounded wait on an mbarrier that
+    nothing arrives at (it must expire)."""
+    ex = ctypes.c_int32()
+    sec = ctypes.c_double()
+    _check(lib.fpt_wait_selftest(ctypes.byref(ex), ctypes.byref(sec), _stream(stream)))
+    return bool(ex.value), sec.value
 
 
 # ---- conveniences (allocation + unpacking; no arithmetic of the method) ----
