@@ -121,3 +121,29 @@ def test_record_capacity_overflow_reported(nat):
     with pytest.raises(nat.FptError) as ei:
         nat.fpt_simulate_mlp(p, sets, 0, N, N.clone(), None)
     assert ei.value.code == nat.FPT_EUNSUPPORTED
+
+
+def test_batch_of_sets_equals_one_call_per_set(nat):
+    """Several parameter sets in one learned-bias launch (different phi_in,
+    walls, steps and caps) give, run for run, exactly the records of one call
+    per set: a run's network input, its noise and its weight depend only on
+    the run, whichever runs share its 128-row tile."""
+    import torch
+    w = nat.mlp_pack(_params(), NORM)
+    specs = [W.SetSpec(phi_in=3.0, m=1.0, b=0.0, dN=1e-3, n_max=6.0, n_traj=3000, phi_uv=4.0, set_id=0),
+             W.SetSpec(phi_in=2.2, m=1.0, b=0.0, dN=2e-3, n_max=4.0, n_traj=1000, set_id=1),
+             W.SetSpec(phi_in=3.5, m=1.0, b=0.0, dN=1e-3, n_max=3.0, n_traj=777, phi_uv=3.6, set_id=5),
+             W.SetSpec(phi_in=1.6, m=1.0, b=0.0, dN=5e-4, n_max=6.0, n_traj=2049, set_id=2)]
+    p = nat.make_params(precision="f32_f64acc", m=1.0, n_max=6.0, mlp=w, k_eval=32)
+    n = sum(s.n_traj for s in specs)
+    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    lw = torch.empty_like(N)
+    nat.fpt_simulate_mlp(p, nat.make_sets(specs), 9, N, lw)
+    off = 0
+    for s in specs:
+        N1 = torch.empty(s.n_traj, dtype=torch.float64, device="cuda")
+        l1 = torch.empty_like(N1)
+        nat.fpt_simulate_mlp(p, nat.make_sets([s]), 9, N1, l1)
+        assert torch.equal(N[off:off + s.n_traj], N1), s.set_id
+        assert torch.equal(lw[off:off + s.n_traj], l1), s.set_id
+        off += s.n_traj
