@@ -99,3 +99,30 @@ def test_polynomial_argument_checks(nat):
     assert ei.value.code == nat.FPT_EINVAL
     with pytest.raises(ValueError):
         nat.make_params(model=nat.MODEL_POLYNOMIAL, poly=[0.0] * 9, n_max=6.0)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_kahan", "f32_f64acc"])
+def test_polynomial_sets_in_one_batch(nat, precision):
+    """Several sets of one potential (different phi_in, phi_end, walls and
+    biases) in one batched launch give exactly the records of one call per
+    set (the coefficients go into every set's constants)."""
+    import torch
+    from paper_2206_11234_gb300 import workloads as W
+    c = [0, 0, 0.5 * 0.3, 0, 0.25 * 0.02]
+    specs = [W.SetSpec(phi_in=3.5, phi_end=1.6, m=0.0, b=0.5, dN=1e-3, n_max=20.0, n_traj=1500, model=2, set_id=0),
+             W.SetSpec(phi_in=3.0, phi_end=1.6, m=0.0, b=0.0, dN=1e-3, n_max=20.0, n_traj=999, phi_uv=3.2,
+                       model=2, set_id=3),
+             W.SetSpec(phi_in=4.0, phi_end=2.0, m=0.0, b=1.0, dN=2e-3, n_max=20.0, n_traj=1024, model=2, set_id=7)]
+    p = nat.make_params(model=nat.MODEL_POLYNOMIAL, precision=precision, poly=c, n_max=20.0)
+    n = sum(s.n_traj for s in specs)
+    N = torch.empty(n, dtype=torch.float64, device="cuda")
+    lw = torch.empty_like(N)
+    nat.fpt_simulate_batch(p, nat.make_sets(specs), 4, N, lw)
+    off = 0
+    for s in specs:
+        N1 = torch.empty(s.n_traj, dtype=torch.float64, device="cuda")
+        l1 = torch.empty_like(N1)
+        nat.fpt_simulate_batch(p, nat.make_sets([s]), 4, N1, l1)
+        assert torch.equal(N[off:off + s.n_traj], N1), s.set_id
+        assert torch.equal(lw[off:off + s.n_traj], l1), s.set_id
+        off += s.n_traj
