@@ -140,3 +140,32 @@ def test_em_delay_of_the_classical_duration():
     se = N.std() / math.sqrt(n)
     assert abs(N.mean() - k1 - delay) < 4 * se, (N.mean() - k1, delay, se)
     assert delay > 30 * se
+
+
+def test_characteristic_function_of_brownian_motion_with_drift():
+    """ln E[e^{iwN}] = (d/s0^2)(|a0| - sqrt(a0^2 - 2 i s0^2 w)) (principal root)."""
+    a0, s0, dist = -1.0, 0.3, 1.0
+    D, S = (lambda x: a0 + 0.0 * x), (lambda x: s0 + 0.0 * x)
+    for w in (0.5, 3.0, 12.0):
+        got = A.log_characteristic_function(w, 1.0 + dist, D, S, 1.0, 1.0 + dist + 6.0)
+        ref = dist / s0 ** 2 * (-a0 - np.sqrt(complex(a0 * a0, -2 * s0 * s0 * w)))
+        assert abs(got - ref) < 1e-8 * abs(ref), (w, got, ref)
+
+
+def test_characteristic_function_matches_cumulants_and_saddle_point():
+    """m = 0.01, phi_in = 6: at small w ln chi = sum_k kappa_k (i w)^k / k! to
+    O(w^5); the Fourier density equals the saddle-point density from -3 to +5
+    sigma (two inversions of the same backward equation)."""
+    D, S = _quad(0.01)
+    k = A.mgf_cumulants(0.0, 6.0, D, S, SQ2, 7.0)
+    w = 2.0
+    series = sum(k[j] * (1j * w) ** j / math.factorial(j) for j in range(1, 5))
+    got = A.log_characteristic_function(w, 6.0, D, S, SQ2, 7.0)
+    assert abs(got - series) < 1e-6, (got, series)
+    sig = math.sqrt(k[2])
+    # dw = 0.3 / sigma puts the aliases 21 sigma away; |chi| < 1e-11 beyond 7.5 / sigma
+    fd = A.FourierDensity(0.3 / sig, 26, lambda x: A.log_characteristic_function(x, 6.0, D, S, SQ2, 7.0))
+    sp = A.SaddlepointDensity.from_mgf(np.arange(-300.0, 326.0, 25.0),
+                                       lambda s: A.mgf_cumulants(s, 6.0, D, S, SQ2, 7.0))
+    N = k[1] + sig * np.array([-3.0, -1.0, 0.0, 1.5, 3.0, 5.0])
+    np.testing.assert_allclose(fd.pdf(N), sp.pdf(N), rtol=2e-4)
