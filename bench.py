@@ -31,8 +31,10 @@ METRIC = ("trajectory steps/s and far-tail effective samples/s at 1 GB300 vs FP6
 # Algorithmic warp-instructions per Euler–Maruyama step of the binary32 stepper
 # (hand count of the work one step needs): Philox 38 per 4 steps (10 rounds of
 # two wide multiplies and the key/word mixing, less the per-run part of round 1),
-# Box–Muller 15 per 2 steps, update + block minimum + noise sum 7.
-ALG_INST_PER_STEP = 38 / 4 + 15 / 2 + 7
+# Box–Muller 15 per 2 steps, and 5.5 for the update in psi = phi / sqrt(2 dN)
+# (reciprocal, one FMA, one add), the noise factor t, half a three-way block
+# minimum and the noise sum.
+ALG_INST_PER_STEP = 38 / 4 + 15 / 2 + 5.5
 MUFU_PER_STEP = 3.0  # lg2 + sqrt + sin + cos per 2 steps, rcp per step
 ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 schedulers)
 MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock

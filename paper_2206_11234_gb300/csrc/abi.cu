@@ -140,6 +140,10 @@ int make_set_const(const fpt_params* p, const fpt_set& s, long long first, SetCo
     c.f_phi_in = (float)s.phi_in;
     c.f_phi_end = (float)s.phi_end;
     c.f_twouv = (float)c.twouv;
+    const double psi_per_phi = 1.0 / std::sqrt(2.0 * s.dN);
+    c.f_psi_in = (float)(psi_per_phi * s.phi_in);
+    c.f_psi_end = (float)(psi_per_phi * s.phi_end);
+    c.f_psi_twouv = (float)(psi_per_phi * c.twouv);
     // binary32 step constants; the noise coefficient carries -sqrt(2 ln 2), the
     // factor between the stepper's Box–Muller radius rho and the normal (rng.cuh)
     const double neg_sqrt2ln2 = -1.1774100225154747;

@@ -46,6 +46,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// minimum of three binary32 values in one instruction (sm_100 and later)
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float y;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+    return y;
+}
 
 
 // ---------------------------------------------------------------------------
@@ -74,6 +80,23 @@ struct ModelStep<float, FPT_MODEL_QUADRATIC> {
         const float inv = rcp_approx(phi);
         const float v = __fmul_rn(m2dN, inv);
         return __fadd_rn(phi, __fmaf_rn(phi, t, v));
+    }
+};
+
+// The same step in the scaled variable psi = phi / sqrt(2 dN), used by the
+// constant-bias stepper: multiplying phi' = phi + phi t - 2 dN / phi by
+// 1/sqrt(2 dN) gives psi' = psi + (psi t - 1/psi), so the drift needs no
+// multiply.  The increment is still formed on its own (one rounding) and then
+// added.  Crossing and wall tests compare psi with the scaled phi_end and
+// 2 phi_uv of the set table; the crossing fraction is scale-free.
+struct QuadPsiStep {
+    float tc, kq;  // as in ModelStep<float, FPT_MODEL_QUADRATIC>
+    __device__ __forceinline__ void load(const SetConst& s) {
+        tc = s.f_c1;
+        kq = s.f_c2;
+    }
+    __device__ __forceinline__ float step(float psi, float t) const {
+        return __fadd_rn(psi, __fmaf_rn(psi, t, -rcp_approx(psi)));
     }
 };
 
@@ -156,6 +179,13 @@ struct ModelStep<float, MODEL> {
     }
 };
 
+// The step a stepper kernel runs: the scaled quadratic step for the binary32
+// constant-bias quadratic model, the model's own step otherwise.
+template <typename Real, int MODEL>
+struct StepOf { using type = ModelStep<Real, MODEL>; };
+template <>
+struct StepOf<float, FPT_MODEL_QUADRATIC> { using type = QuadPsiStep; };
+
 // Four binary32 EM steps of a power model: as steps4_f32, with the block's
 // log-weight summed step by step into acc.
 template <int MODEL, bool WALL>
@@ -170,18 +200,26 @@ __device__ __forceinline__ void steps4_pow(const ModelStep<float, MODEL>& model,
         const float q = __fmul_rn(model.kq, np.rho);
         phi = model.advance(phi, q, np.c, acc);
         if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        mn = fminf(mn, phi);
+        const float first = phi;
         phi = model.advance(phi, q, np.s, acc);
         if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        mn = fminf(mn, phi);
+        mn = min3f(mn, first, phi);
     }
 }
 
+// One binary32 EM step and the wall.
+template <bool WALL, typename Step>
+__device__ __forceinline__ float step1_f32(const Step& model, float phi, float t, float twouv) {
+    phi = model.step(phi, t);
+    if constexpr (WALL) phi = fminf(phi, twouv - phi);
+    return phi;
+}
+
 // Four binary32 EM steps from one Philox block (two Box–Muller pairs): the
-// state update, the wall, the block minimum and the running sum of
-// rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
-template <int MODEL, bool WALL>
-__device__ __forceinline__ void steps4_f32(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t k,
+// state update, the wall, the block minimum (one three-way minimum per pair)
+// and the running sum of rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
+template <bool WALL, typename Step>
+__device__ __forceinline__ void steps4_f32(const Step& model, const PhiloxLane& pl, uint32_t k,
                                            const PhiloxKeys& keys, float twouv, float& phi, float& mn,
                                            float& srho) {
     uint32_t w[4];
@@ -190,12 +228,10 @@ __device__ __forceinline__ void steps4_f32(const ModelStep<float, MODEL>& model,
     for (int p = 0; p < 2; ++p) {
         const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
         const float q = __fmul_rn(model.kq, np.rho);
-        phi = model.step(phi, __fmaf_rn(q, np.c, model.tc));
-        if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        mn = fminf(mn, phi);
-        phi = model.step(phi, __fmaf_rn(q, np.s, model.tc));
-        if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        mn = fminf(mn, phi);
+        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.c, model.tc), twouv);
+        const float first = phi;
+        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.s, model.tc), twouv);
+        mn = min3f(mn, first, phi);
         srho = __fmaf_rn(np.rho, np.c + np.s, srho);
     }
 }
@@ -343,12 +379,26 @@ __device__ __forceinline__ float real_min<float>(float a, float b) { return fmin
 template <>
 __device__ __forceinline__ double real_min<double>(double a, double b) { return fmin(a, b); }
 
-template <typename Real>
-__device__ __forceinline__ Real set_phi_in(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_phi_in : (Real)S.phi_in; }
-template <typename Real>
-__device__ __forceinline__ Real set_phi_end(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_phi_end : (Real)S.phi_end; }
-template <typename Real>
-__device__ __forceinline__ Real set_twouv(const SetConst& S) { return sizeof(Real) == 4 ? (Real)S.f_twouv : (Real)S.twouv; }
+// phi_in, phi_end and 2 phi_uv in the stepper's state variable: binary64 phi,
+// binary32 phi, or binary32 psi = phi / sqrt(2 dN) for the quadratic constant-bias step
+template <typename Real, int MODEL>
+__device__ __forceinline__ Real set_phi_in(const SetConst& S) {
+    if constexpr (sizeof(Real) == 8) return (Real)S.phi_in;
+    else if constexpr (MODEL == FPT_MODEL_QUADRATIC) return S.f_psi_in;
+    else return S.f_phi_in;
+}
+template <typename Real, int MODEL>
+__device__ __forceinline__ Real set_phi_end(const SetConst& S) {
+    if constexpr (sizeof(Real) == 8) return (Real)S.phi_end;
+    else if constexpr (MODEL == FPT_MODEL_QUADRATIC) return S.f_psi_end;
+    else return S.f_phi_end;
+}
+template <typename Real, int MODEL>
+__device__ __forceinline__ Real set_twouv(const SetConst& S) {
+    if constexpr (sizeof(Real) == 8) return (Real)S.twouv;
+    else if constexpr (MODEL == FPT_MODEL_QUADRATIC) return S.f_psi_twouv;
+    else return S.f_twouv;
+}
 
 // A run that finished inside its last block, waiting for the replay.
 template <typename Real, int PREC>
@@ -411,10 +461,10 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
     if ((int)lane >= cnt) return;
     const Pending<Real, PREC> e = q[lane];
     const SetConst& S = s_sets[e.set];
-    ModelStep<Real, MODEL> model;
+    typename StepOf<Real, MODEL>::type model;
     model.load(S);
-    const Real phi_end = set_phi_end<Real>(S);
-    const Real twouv = set_twouv<Real>(S);
+    const Real phi_end = set_phi_end<Real, MODEL>(S);
+    const Real twouv = set_twouv<Real, MODEL>(S);
     const PhiloxLane pl = philox_lane(S.traj_offset + (e.rec - (unsigned long long)S.first), S.set_id, P.keys);
     Real ph = e.phi0, prev = e.phi0, s2 = (Real)0;
     int M = 0;
@@ -436,10 +486,10 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
                         if constexpr (is_pow_model(MODEL)) {
                             ph = model.advance(ph, q, trig, s2);
                         } else {
-                            ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                            ph = step1_f32<WALL>(model, ph, __fmaf_rn(q, trig, model.tc), twouv);
                             s2 = __fmaf_rn(np.rho, trig, s2);
                         }
-                        if constexpr (WALL) ph = fminf(ph, twouv - ph);
+                        if constexpr (WALL && is_pow_model(MODEL)) ph = fminf(ph, twouv - ph);
                         const int step_index = e.m0 + 4 * g + 2 * p + h;
                         if (ph <= phi_end) {
                             crossed = true;
@@ -543,7 +593,7 @@ stepper_kernel(const StepperParams P) {
     Real phi = (Real)0, phi_end = (Real)0, twouv = (Real)0;
     int m = 0, m_max = 0;
     PhiloxLane pl{0u, 0u, 0u};
-    ModelStep<Real, MODEL> model;
+    typename StepOf<Real, MODEL>::type model;
     model.load(s_sets[0]);
     WSum<PREC> W;
     W.reset();
@@ -576,9 +626,9 @@ stepper_kernel(const StepperParams P) {
                     rec = t;
                     pl = philox_lane(S.traj_offset + (t - (unsigned long long)S.first), S.set_id, P.keys);
                     model.load(S);
-                    phi = set_phi_in<Real>(S);
-                    phi_end = set_phi_end<Real>(S);
-                    twouv = set_twouv<Real>(S);
+                    phi = set_phi_in<Real, MODEL>(S);
+                    phi_end = set_phi_end<Real, MODEL>(S);
+                    twouv = set_twouv<Real, MODEL>(S);
                     m = 0;
                     m_max = S.m_max;
                     W.reset();
@@ -605,7 +655,7 @@ stepper_kernel(const StepperParams P) {
             if constexpr (sizeof(Real) == 4 && is_pow_model(MODEL)) {
                 steps4_pow<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
             } else if constexpr (sizeof(Real) == 4) {
-                steps4_f32<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
+                steps4_f32<WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
             } else {
                 Real xi[4];
                 normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
@@ -675,8 +725,8 @@ stepper_kernel(const StepperParams P) {
                 pl.r1_set = unpark(v, 10 * stride);
                 const SetConst& S = s_sets[set];
                 model.load(S);
-                phi_end = set_phi_end<Real>(S);
-                twouv = set_twouv<Real>(S);
+                phi_end = set_phi_end<Real, MODEL>(S);
+                twouv = set_twouv<Real, MODEL>(S);
                 m_max = S.m_max;
             }
         }

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams
         const uint32_t k0 = (uint32_t)m0 >> 2;
 #pragma unroll
         for (int g = 0; g < KS / 4; ++g)
-            steps4_f32<FPT_MODEL_QUADRATIC, true>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
+            steps4_f32<true>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
         const float sblk = -kSqrt2Ln2 * srho;  // the block's sum of normals
         m = m0 + KS;
         const bool event = live && (mn <= phi_end || m >= m_max);

@@ -29,6 +29,9 @@ struct SetConst {
     int m_max;                              // censoring cap in steps
     uint32_t set_id;                        // Philox counter word 3
     float f_phi_in, f_phi_end, f_twouv;
+    // the same three in the binary32 state variable of the quadratic constant-bias
+    // stepper, psi = phi / sqrt(2 dN) (stepper.cuh, QuadPsiStep)
+    float f_psi_in, f_psi_end, f_psi_twouv;
     float f_c1, f_c2, f_c3;                 // binary32 step constants (see ModelStep)
     float f_cmdN;                           // c0 m dN: the bias part of dphi/phi is b * f_cmdN
     float f_dN, f_sq;                       // dN and sqrt(dN) in binary32 (learned-bias stepper)
