@@ -28,16 +28,18 @@ sys.path.insert(0, ROOT)
 METRIC = ("trajectory steps/s and far-tail effective samples/s at 1 GB300 vs FP64 plain; "
           "% issue roofline")
 
-# Algorithmic warp-instructions per Euler–Maruyama step of the binary32 stepper
-# (hand count of the work one step needs): Philox 38 per 4 steps (10 rounds of
-# two wide multiplies and the key/word mixing, less the per-run part of round 1),
-# Box–Muller 15 per 2 steps, and 5.5 for the update in psi = phi / sqrt(2 dN)
-# (reciprocal, one FMA, one add), the noise factor t, half a three-way block
-# minimum and the noise sum.
-ALG_INST_PER_STEP = 38 / 4 + 15 / 2 + 5.5
+# Algorithmic work per Euler–Maruyama step of the binary32 stepper (hand
+# count of what one step needs, in warp-instructions per warp-step of 32 runs):
+# Philox 38 per counter (10 rounds of two wide multiplies and the key/word
+# mixing, less the per-run part of round 1), three counters per 16 steps;
+# Box–Muller 16 per pair of steps (uniform and radius 4, angle word and angle
+# 6 with the sine and cosine, the noise factor, the noise sum 2, ...); and 5.5
+# for the update in psi = phi / sqrt(2 dN) (reciprocal, one FMA, one add), the
+# noise term t, half a three-way block minimum and the noise sum.
+ALG_INST_PER_STEP = 3 * 38 / 16 + 13 / 2 + 5.5
 MUFU_PER_STEP = 3.0  # lg2 + sqrt + sin + cos per 2 steps, rcp per step
+WIDE_MUL_PER_STEP = 3 * 19 / 16  # 32x32->64 multiplies: 19 per Philox counter (round 1 folds one)
 ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 schedulers)
-MUFU_PER_SM_CLK = 0.5  # 16 lanes per SM per clock
 # learned bias: per run and evaluation, 2 x 64 tanh on the XU pipe and
 # 2*64 + 64*64 + 64 multiply-adds (2 -> 64 -> 64 -> 1) on the tensor cores
 MLP_TANH_PER_EVAL = 128
@@ -46,7 +48,8 @@ MLP_MAC_PER_EVAL = 2 * 64 + 64 * 64 + 64
 
 # Sources the binary32 stepper kernel is built from: DRAM counters recorded
 # for it in profiles/ apply only while these files are unchanged.
-STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h", "../build.py")
+STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_f64.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h",
+                   "../build.py")
 
 
 def stepper_source_hash() -> str:
@@ -59,19 +62,19 @@ def stepper_source_hash() -> str:
     return h.hexdigest()
 
 
-def stepper_counters(precision, block_dim, k_steps):
-    """The ncu counters recorded for the binary32 stepper in
-    profiles/stepper_counters.json (DRAM bytes, instructions, branch and lane
-    efficiency of one launch over a stated number of runs and steps), or None
-    when no record matches this kernel, launch shape and source."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "stepper_counters.json")
+def stepper_counters(precision, block_dim, k_steps, name="stepper_counters.json"):
+    """The ncu counters recorded for a stepper kernel in profiles/ (DRAM bytes,
+    instructions, pipe activity, branch and lane efficiency of one launch over
+    a stated number of runs and steps), or None when no record matches this
+    kernel's precision, launch shape (threads per block and block length) and
+    source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", name)
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    # the executed code depends on the precision and block length, not on the block size
-    if (rec.get("precision"), rec.get("k_steps")) != (precision, k_steps):
+    if (rec.get("precision"), rec.get("block_dim"), rec.get("k_steps")) != (precision, block_dim, k_steps):
         return None
     if rec.get("source_sha256") != stepper_source_hash():
         return None
@@ -96,6 +99,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="default workload: skip the learned-bias experiment")
     ap.add_argument("--block-dim", type=int, default=0)
     ap.add_argument("--k-steps", type=int, default=0)
     return ap.parse_args()
@@ -219,15 +223,16 @@ def cpu_oracle_rate(workload, seconds, threads=None):
     return tally["steps"] / dt, threads, sample
 
 
-def run_learned_bias(args):
+def learned_bias_experiment(args, rates=None):
     """Learned bias vs the best constant bias on far-tail effective samples per
     second: m = 1, phi_in = 8, reflecting wall phi_uv = 9, dN = 5e-4, tail event
     N > 40, censored at N = 60.  A ladder of constant b (2^20 runs each) picks
     the best b by effective samples per EM step; that b is rerun on as many
     runs as the learned inference (2^26) for a like-for-like n_eff/s.  Training:
-    2^16 runs per Adam step, --train-steps steps (2^24 runs at the default).
-    Everything is scaled by --scale.  The FP64 oracle runs the trained network
-    on a bounded sample as a cross-check of the estimate."""
+    2^16 runs per Adam step, --train-steps steps (2^24 runs at the default),
+    timed on the host clock around the device-synchronised loop.  Everything
+    is scaled by --scale.  The FP64 oracle runs the trained network on a
+    bounded sample as a cross-check of the estimate.  Returns a dict."""
     import torch
     from paper_2206_11234_gb300 import native as nat
     from paper_2206_11234_gb300 import workloads as W
@@ -237,6 +242,7 @@ def run_learned_bias(args):
     stream = torch.cuda.current_stream(dev)
     base = dict(phi_in=8.0, m=1.0, dN=5e-4, n_max=60.0, phi_uv=9.0)
     tail = 40.0
+    p_ref = 1.0986e-3  # survival PDE (continuum limit)
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,7 +275,8 @@ def run_learned_bias(args):
     ladder = [constant(b, n_c, 11) for b in (0.0, 0.2, 0.4, 0.6, 0.8, 1.0, 2.0, 4.0, 6.0)]
     best_b = max(ladder, key=lambda r: r["n_eff_per_Msteps"])["b"]
     n_i = max(4096, int((1 << 26) * args.scale))
-    best = constant(best_b, n_i, 13)
+    with ClockSampler(0) as clk_c:
+        best = constant(best_b, n_i, 13)
     # training, starting from the best constant amplitude
     n_t = max(1024, int((1 << 16) * args.scale))
     init = W.mlp_params(seed=5, gain=1.0, out_scale=0.05)
@@ -281,6 +288,7 @@ def run_learned_bias(args):
     t0 = time.perf_counter()
     for it in range(args.train_steps):
         hist.append(tr.step(seed=100000 + it, tail_N=tail, lr=args.lr))
+    torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # inference with the trained network
     spec = W.SetSpec(n_traj=n_i, b=0.0, **base)
@@ -292,13 +300,15 @@ def run_learned_bias(args):
     warm = nat.make_sets([W.SetSpec(n_traj=min(n_i, 65536), b=0.0, **base)])
     nat.fpt_simulate_mlp(p, warm, 77, N, lw)  # warm-up
     steps.zero_()
-    _, t_inf = timed(lambda: nat.fpt_simulate_mlp(p, sets, 12345, N, lw))
+    with ClockSampler(0) as clk_l:
+        _, t_inf = timed(lambda: nat.fpt_simulate_mlp(p, sets, 12345, N, lw))
     ne = tail_neff(N, lw, [spec], tail)[0]
     st = int(steps.item())
-    learned = {"runs": n_i, "P": ne["P"], "n_eff": ne["n_eff"], "seconds": t_inf, "steps": st,
+    se_gpu = math.sqrt(max(ne["P"] ** 2 / max(ne["n_eff"], 1e-300), 0.0))
+    learned = {"runs": n_i, "P": ne["P"], "se": se_gpu, "n_eff": ne["n_eff"], "seconds": t_inf, "steps": st,
                "steps_per_s": st / t_inf, "n_eff_per_s": ne["n_eff"] / t_inf,
                "n_eff_per_Msteps": 1e6 * ne["n_eff"] / st,
-               "train_seconds": train_s, "train_runs": n_t * args.train_steps,
+               "train_seconds": train_s, "train_runs": n_t * args.train_steps, "train_steps": args.train_steps,
                "rel_second_moment_log_first": hist[0]["log_second_moment"] - 2 * math.log(max(hist[0]["p_hat"], 1e-300)),
                "rel_second_moment_log_last": hist[-1]["log_second_moment"] - 2 * math.log(max(hist[-1]["p_hat"], 1e-300))}
     # roofline of the learned-bias stepper: the XU (MUFU) pipe binds, with the
@@ -309,14 +319,18 @@ def run_learned_bias(args):
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     mufu_per_step = MUFU_PER_STEP + MLP_TANH_PER_EVAL / args.k_eval
     mufu_rate = learned["steps_per_s"] / 32 * mufu_per_step
-    mufu_peak = n_sm * MUFU_PER_SM_CLK * f_max
+    if rates:
+        mufu_peak = rates["xu_lg2_per_s"] / 32
+        src = "XU pipe measured in this run (fpt_pipe_rates: lg2.approx loop on every SM)"
+    else:
+        mufu_peak = n_sm * 0.5 * f_max
+        src = f"{n_sm} SMs x 16 MUFU lanes/clk x {f_max / 1e6:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"
     tflops = learned["steps_per_s"] * 2 * MLP_MAC_PER_EVAL / args.k_eval / 1e12
     bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
     roofline = {"bound": "alu", "achieved": mufu_rate / 1e9, "peak": mufu_peak / 1e9,
                 "unit": "Gwarp-MUFU/s (algorithmic, XU pipe)", "frac": mufu_rate / mufu_peak, "traffic": None,
-                "kernel": f"stepper_mlp_kernel<{args.k_eval}>",
-                "mufu_per_warp_step": mufu_per_step,
-                "peak_source": f"{n_sm} SMs x 16 MUFU lanes/clk x {f_max / 1e6:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+                "kernel": f"stepper_mlp_kernel<{args.k_eval}>", "mufu_per_warp_step": mufu_per_step,
+                "peak_source": src,
                 "tensor_term": {"achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s (bf16)",
                                 "frac": tflops / bf16_peak if bf16_peak else None,
                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS)"}}
@@ -340,18 +354,33 @@ def run_learned_bias(args):
     xo = np.where(No > tail, np.exp(lo), 0.0)
     orc = {"runs": n_o, "P": float(xo.mean()), "se": float(xo.std() / math.sqrt(n_o)),
            "seconds": time.perf_counter() - t0}
-    se_gpu = math.sqrt(max(ne["P"] ** 2 / max(ne["n_eff"], 1e-300), 0.0))
-    line = {"metric": METRIC, "value": learned["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": 1,
-            "warmup": 1, "ms_per_step": 1e3 * t_inf, "higher_is_better": True, "scaling": "weak",
+    return {"event": f"N > {tail}", "reference_P_survival_pde": p_ref,
+            "learned_vs_pde_rel": learned["P"] / p_ref - 1.0,
+            "best_constant": best, "learned": learned, "oracle_learned": orc,
+            "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None,
+            "roofline": roofline, "ladder": ladder,
+            "constant_launch_shape": {"block_dim": tuned[0], "k_steps": tuned[1]},
+            "k_eval": args.k_eval, "scale": args.scale, "lr": args.lr,
+            "clocks": {"learned": clk_l.summary(), "best_constant": clk_c.summary()}}
+
+
+def run_learned_bias(args):
+    import torch
+    from paper_2206_11234_gb300 import native as nat
+    torch.cuda.set_device(0)
+    rates = nat.fpt_pipe_rates()
+    r = learned_bias_experiment(args, rates)
+    L = r["learned"]
+    line = {"metric": METRIC, "value": L["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * L["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "learned bias vs constant: m=1 phi_in=8 phi_uv=9 dN=5e-4, tail N > 40",
                        "scale": args.scale, "train_steps": args.train_steps, "lr": args.lr,
-                       "k_eval": args.k_eval,
-                       "constant_launch_shape": {"block_dim": tuned[0], "k_steps": tuned[1]}},
-            "tail": {"event": f"N > {tail}", "reference_P_survival_pde": 1.0986e-3,
-                     "best_constant": best, "learned": learned, "learned_se": se_gpu, "oracle_learned": orc,
-                     "gain_n_eff_per_s": learned["n_eff_per_s"] / best["n_eff_per_s"] if best["n_eff_per_s"] else None},
-            "roofline": roofline, "ladder": ladder}
+                       "k_eval": args.k_eval, "constant_launch_shape": r["constant_launch_shape"]},
+            "clocks": r["clocks"]["learned"], "pipe_rates": rates,
+            "tail": {k: r[k] for k in ("event", "reference_P_survival_pde", "best_constant", "learned",
+                                       "oracle_learned", "gain_n_eff_per_s")},
+            "roofline": r["roofline"], "ladder": r["ladder"]}
     print(json.dumps(line))
 
 
@@ -592,6 +621,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
 
+    # measured pipe rates of this GPU (the denominators of the rooflines below)
+    rates = nat.fpt_pipe_rates()
     wl = make_workload(args.workload, args.scale)
     # weak scaling: each rank simulates its own disjoint id range of every set
     for s in wl.sets:
@@ -677,6 +708,21 @@ def main():
         ms_max, total_steps = ms, float(my_steps)
     value = total_steps / (ms_max / 1e3)
 
+    # the per-rank histograms of the last timed step merged into the histogram of
+    # the whole job (gather over the process group, fpt_hist_merge on the host;
+    # the counters are integers and add): outside the timed region
+    hist_merge = None
+    if world > 1:
+        from paper_2206_11234_gb300 import shard
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        merged_bins, _ = shard.allgather_merge(bins)
+        merged_counts = counts.clone()
+        dist.all_reduce(merged_counts, op=dist.ReduceOp.SUM)
+        hist_merge = {"ranks": world, "bins": nbins, "seconds": time.perf_counter() - t0,
+                      "runs": int(merged_counts[:, 3].sum().item()),
+                      "in_range": int(merged_bins.numpy().view(np.int64)[:, 7].sum())}
+
     # the stepper kernel alone (CUDA events on the launching stream), for the roofline
     ms_stepper = None
     if rank == 0:
@@ -686,20 +732,36 @@ def main():
         stepper_steps = int(steps_ctr.item()) / args.steps
 
     extra = {}
+    if hist_merge is not None:
+        extra["hist_merge"] = hist_merge
     if rank == 0:
         # far-tail effective samples (E = {N > tail_N}) of the last timed step's runs
         plan.launch(args.steps - 1, stream)
         if wl.tail_N is not None:
             ne = tail_neff(N, lw, specs, wl.tail_N)
-            best = max(ne, key=lambda r: r["n_eff"])
+            # each set's share of the step time: its EM steps (from the records: the
+            # crossing step ceil(N/dN), or the cap ceil(n_max/dN) when censored) over all
+            t_step = ms_max / 1e3 / args.steps
+            off = 0
+            for s_, r_ in zip(specs, ne):
+                Ns = N[off:off + s_.n_traj]
+                cap = float(math.ceil(s_.n_max / s_.dN))
+                r_["steps"] = torch.where(torch.isfinite(Ns), torch.ceil(Ns / s_.dN), torch.full_like(Ns, cap)).sum().item()
+                off += s_.n_traj
+            tot = sum(r_["steps"] for r_ in ne) or 1.0
+            for r_ in ne:
+                r_["seconds"] = t_step * r_["steps"] / tot
+                r_["n_eff_per_s"] = r_["n_eff"] / r_["seconds"] if r_["seconds"] > 0 else 0.0
+            best = max(ne, key=lambda r: r["n_eff_per_s"])
             extra["tail"] = {"event": f"N > {wl.tail_N}", "per_set": ne,
-                             "best_n_eff_per_s": best["n_eff"] / (ms_max / 1e3 / args.steps),
-                             "best_b": best["b"]}
+                             "best_n_eff_per_s": best["n_eff_per_s"], "best_b": best["b"],
+                             "time_share": "each set's n_eff over its share of the step time (its EM steps / all)"}
         # FP64 GPU plain on a bounded sample of the same workload (speed reference)
         if not args.no_f64:
             frac = min(1.0, 2**16 * len(specs) / n)
             wl64 = make_workload(args.workload, args.scale * frac)
-            p64 = params("f64", steps_ctr)
+            p64 = nat.make_params(model=s0.model, precision="f64", m=s0.m, a0=s0.a0, s0=s0.s0, n_max=s0.n_max,
+                                  block_dim=256, k_steps=4, stream=stream, steps_out=steps_ctr)
             n64 = wl64.n_total
             N64 = torch.empty(n64, dtype=torch.float64, device=dev)
             l64 = torch.empty(n64, dtype=torch.float64, device=dev)
@@ -713,7 +775,7 @@ def main():
             b_.record(stream)
             torch.cuda.synchronize()
             extra["f64_gpu_plain"] = {"value": int(steps_ctr.item()) / (a.elapsed_time(b_) / 1e3),
-                                      "unit": "steps/s", "runs": n64}
+                                      "unit": "steps/s", "runs": n64, "block_dim": 256, "k_steps": 4}
             del N64, l64
 
     # end to end through the host-buffer entry (pinned host memory)
@@ -757,49 +819,78 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    issue_peak = n_sm * ISSUE_PER_SM_CLK * f_max  # warp-instructions/s
-    mufu_peak = n_sm * MUFU_PER_SM_CLK * f_max  # warp-MUFU operations/s
-    issue_steps_peak = issue_peak / ALG_INST_PER_STEP * 32
-    mufu_steps_peak = mufu_peak / MUFU_PER_STEP * 32
-    steps_peak = min(issue_steps_peak, mufu_steps_peak)
+    # three pipes bound the binary32 step: instruction issue (1 per SM
+    # sub-partition per clock), the XU pipe (MUFU) and the fma-heavy pipe (the
+    # Philox wide multiplies); the XU and wide-multiply peaks are measured in
+    # this run by the library's pipe-rate loops (thread operations per second)
+    issue_peak = n_sm * ISSUE_PER_SM_CLK * f_max           # warp-instructions/s
+    mufu_peak = rates["xu_lg2_per_s"] / 32                  # warp-MUFU/s
+    wide_peak = rates["wide_mul_per_s"] / 32                # warp wide multiplies/s
+    bounds = {"issue": issue_peak / ALG_INST_PER_STEP * 32, "xu": mufu_peak / MUFU_PER_STEP * 32,
+              "fma_heavy": wide_peak / WIDE_MUL_PER_STEP * 32}
+    binding = min(bounds, key=bounds.get)
+    steps_peak = bounds[binding]
     achieved_steps = stepper_steps / (ms_stepper / 1e3)
     shape = tuned or {"block_dim": args.block_dim, "k_steps": args.k_steps}
     ctr = stepper_counters(wl.precision, shape.get("block_dim"), shape.get("k_steps"))
     measured = None
     if ctr:
-        inst_ws = ctr["inst_executed"] / (ctr["steps"] / 32.0)  # warp-instructions per warp-step
+        ws = ctr["steps"] / 32.0
+        inst_ws = ctr["inst_executed"] / ws  # warp-instructions per warp-step
         measured = {"inst_per_warp_step": inst_ws,
                     "steps_per_s_peak": issue_peak / inst_ws * 32,
                     "frac": achieved_steps / (issue_peak / inst_ws * 32),
+                    "xu_inst_per_warp_step": ctr.get("inst_xu", 0) / ws,
+                    "fma_heavy_cycles_per_warp_step": ctr.get("fmaheavy_cycles", 0) / (4 * n_sm) / (ws / (4 * n_sm)),
+                    "pipe_busy_pct": ctr.get("pipe_busy_pct"),
                     "branch_targets_uniform_pct": ctr["branch_targets_uniform_pct"],
                     "active_lanes_per_inst_pct": 100.0 * ctr["thread_inst_executed"] / (32.0 * ctr["inst_executed"]),
                     "source": "profiles/stepper_counters.json"}
-    # reported against the binding one of the two co-bounds (issue slots, XU pipe)
-    if mufu_steps_peak <= issue_steps_peak:
-        a_, p_, u_ = achieved_steps * MUFU_PER_STEP / 32 / 1e9, mufu_peak / 1e9, "Gwarp-MUFU/s (algorithmic, XU pipe)"
-    else:
-        a_, p_, u_ = achieved_steps * ALG_INST_PER_STEP / 32 / 1e9, issue_peak / 1e9, "Gwarp-inst/s (algorithmic)"
-    roof = {"bound": "alu", "achieved": a_, "peak": p_, "unit": u_, "frac": a_ / p_,
-            "issue_term": {"achieved": achieved_steps * ALG_INST_PER_STEP / 32 / 1e9, "peak": issue_peak / 1e9,
-                           "unit": "Gwarp-inst/s", "frac": achieved_steps / issue_steps_peak,
-                           "inst_per_warp_step": ALG_INST_PER_STEP},
-            "xu_term": {"achieved": achieved_steps * MUFU_PER_STEP / 32 / 1e9, "peak": mufu_peak / 1e9,
-                        "unit": "Gwarp-MUFU/s", "frac": achieved_steps / mufu_steps_peak,
-                        "mufu_per_warp_step": MUFU_PER_STEP},
+    units = {"issue": ("Gwarp-inst/s (algorithmic)", ALG_INST_PER_STEP, issue_peak),
+             "xu": ("Gwarp-MUFU/s (algorithmic, XU pipe)", MUFU_PER_STEP, mufu_peak),
+             "fma_heavy": ("Gwarp-wide-multiplies/s (algorithmic, fma-heavy pipe)", WIDE_MUL_PER_STEP, wide_peak)}
+
+    def term(name):
+        u, per, pk_ = units[name]
+        return {"achieved": achieved_steps * per / 32 / 1e9, "peak": pk_ / 1e9, "unit": u,
+                "frac": achieved_steps / bounds[name], "per_warp_step": per, "steps_per_s_bound": bounds[name]}
+    u_, per_, p_ = units[binding]
+    roof = {"bound": "alu", "binding_pipe": binding, "achieved": achieved_steps * per_ / 32 / 1e9, "peak": p_ / 1e9,
+            "unit": u_, "frac": achieved_steps / steps_peak,
+            "issue_term": term("issue"), "xu_term": term("xu"), "fma_heavy_term": term("fma_heavy"),
             "traffic": (ctr["dram_read_bytes"] + ctr["dram_write_bytes"]) * n / ctr["runs"] if ctr else None,
             "vs_measured_instructions": measured,
             "kernel": f"stepper_kernel<float, {wl.precision}, quadratic, "
-                      f"k_steps {(tuned or {}).get('k_steps', args.k_steps)}>",
+                      f"block_dim {shape.get('block_dim')}, k_steps {shape.get('k_steps')}>",
             "steps_per_s": achieved_steps, "steps_per_s_peak": steps_peak,
-            "peak_source": f"{n_sm} SMs x 4 issue/clk and x 16 MUFU lanes/clk, x {f_max / 1e6:.0f} MHz "
-                           "(max SM clock, MEASURED_PEAKS.json)"}
+            "peak_source": (f"issue: {n_sm} SMs x 4 issue/clk x {f_max / 1e6:.0f} MHz (max SM clock, "
+                            "MEASURED_PEAKS.json); XU and fma-heavy: measured in this run by fpt_pipe_rates "
+                            "(one-instruction loops on every SM)")}
     if wl.precision == "f64":
-        # the binary64 reference path (per-run parity configuration): no FP64 peak
-        # is measured on this machine and the FP32 issue roofline does not apply
+        # the binary64 reference path (per-run parity configuration)
         roof = {"bound": "fp64", "achieved": achieved_steps, "peak": None, "unit": "steps/s", "frac": None,
                 "traffic": None, "kernel": f"stepper_kernel<double, f64, {wl.sets[0].model and 'constant' or 'quadratic'}, "
                                            f"k_steps {shape.get('k_steps')}>",
-                "note": "binary64 reference path; no roofline fraction is claimed"}
+                "note": "binary64 reference path: its FP64-pipe fraction is in f64_gpu_plain.roofline of the "
+                        "binary32 workloads' lines"}
+    if "f64_gpu_plain" in extra:
+        # FP64 roofline: FP64-pipe warp-instructions per warp-step (ncu record of the
+        # binary64 stepper) x the live rate, against the measured DFMA rate
+        f64 = extra["f64_gpu_plain"]
+        c64 = stepper_counters("f64", f64.get("block_dim"), f64.get("k_steps"), name="stepper_f64_counters.json")
+        fp64_peak = rates["fp64_fma_per_s"] / 32  # warp DFMA/s
+        if c64:
+            per = c64["inst_fp64"] / (c64["steps"] / 32.0)
+            ach = f64["value"] / 32 * per
+            f64["roofline"] = {"bound": "fp64", "achieved": ach / 1e9, "peak": fp64_peak / 1e9,
+                               "unit": "Gwarp-FP64-inst/s", "frac": ach / fp64_peak,
+                               "fp64_inst_per_warp_step": per, "steps_per_s_bound": fp64_peak / per * 32,
+                               "pipe_busy_pct_ncu": c64.get("fp64_pipe_busy_pct"),
+                               "peak_source": "DFMA loop on every SM in this run (fpt_pipe_rates)",
+                               "source": "profiles/stepper_f64_counters.json"}
+        else:
+            f64["roofline"] = {"bound": "fp64", "peak": fp64_peak / 1e9, "unit": "Gwarp-DFMA/s", "frac": None,
+                               "note": "no ncu record of the FP64-pipe instructions for this kernel and shape"}
     cpu = None
     if not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -830,7 +921,13 @@ def main():
         "context": "the paper's CPU package (Python) reports ~8 h for 2e5 drift-dominated runs on a quad-core "
                    "laptop and 'a few hours on a single CPU' for the whole study; it gives no steps/s",
     }
+    line["pipe_rates"] = dict(rates, per_sm_clock={k: v / (n_sm * f_max) for k, v in rates.items()},
+                              clock_assumed_mhz=f_max / 1e6)
     line.update(extra)
+    if world == 1 and args.workload == "drift_ladder" and not args.no_learned:
+        # the learned-bias configuration (m = 1, phi_in = 8, wall 9, tail N > 40):
+        # learned vs best constant bias on far-tail effective samples per second
+        line["learned_bias"] = learned_bias_experiment(args, rates)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

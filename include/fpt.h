@@ -34,12 +34,15 @@
  *     detected on the host before any GPU work is enqueued.  fpt_strerror()
  *     names a code; fpt_last_error() describes the last failure of the calling
  *     thread.
- *   - Random numbers: xi for steps 4k..4k+3 of trajectory i come from one
- *     Philox4x32-10 block (Salmon et al., SC'11) with counter
- *     (k, i_lo, i_hi, set_id) and key (seed_lo, seed_hi), mapped to normals by
- *     Box–Muller.  Any run can be reproduced from (seed, set_id, i) alone, so
- *     an id range can be split across calls or GPUs (traj_offset) with
- *     bit-identical results.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
+ *     (c, i_lo, i_hi, set_id) and key (seed_lo, seed_hi), mapped to normals by
+ *     Box–Muller with 48 bits per pair of normals.  Steps 16G .. 16G + 15 of
+ *     trajectory i use the twelve words of counters c = 3G, 3G + 1, 3G + 2;
+ *     steps 16G + 4j .. 16G + 4j + 3 take words 3j and 3j + 1 (radius words
+ *     of their two pairs) and 3j + 2 (the two 16-bit angles, first pair in
+ *     the high half).  Any run can be reproduced from (seed, set_id, i)
+ *     alone, so an id range can be split across calls or GPUs (traj_offset)
+ *     with bit-identical results.
  *   - A run still inflating after ceil(n_max/dN) steps is censored: N = +inf,
  *     ln w = its weight at that step (E[w] = 1 still holds).
  */
@@ -52,7 +55,7 @@
 extern "C" {
 #endif
 
-#define FPT_ABI_VERSION 2 /* 2: fpt_bin carries four moments of ln w; fpt_estimate */
+#define FPT_ABI_VERSION 3 /* 2: fpt_bin carries four moments of ln w; fpt_estimate; 3: bias terms of the lognormal estimate */
 
 /* return codes */
 #define FPT_OK 0
@@ -201,6 +204,20 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
 
+/* Merge of weighted histograms of disjoint sets of runs (shards of one
+ * workload on several GPUs, or calls over split id ranges: runs are
+ * independent, §2.1) into the histogram of their union, in binary64 on the
+ * host.  parts: host array of n_parts x n_bins bins, part p's bins at
+ * parts + p * n_bins, all with the same bin edges; out: n_bins host bins
+ * (may not alias parts).  Each part is moved to the common max_lw M of its
+ * bin, d = max_lw - M <= 0: s1 e^d, s2 e^(2d), l_k -> sum_i C(k,i) d^(k-i) l_i
+ * (l_0 = count), then summed; empty parts (max_lw = -inf) add nothing.
+ * part_counts / out_counts (nullable together): the counters, summed.
+ * Bins with max_lw NaN or a negative count are rejected (FPT_EINVAL).  No GPU
+ * work; callable without a device. */
+int fpt_hist_merge(const fpt_bin* parts, int32_t n_parts, int64_t n_bins, const fpt_hist_counts* part_counts,
+                   fpt_bin* out, fpt_hist_counts* out_counts);
+
 /* Per-bin estimates of the first-passage-time density from a histogram
  * (fpt_estimate).  d = bin width, n_total = runs of the histogram (all of
  * them: in range, out of range and censored).
@@ -215,12 +232,23 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
  *                         p-value exp(-K^2/2) (the normality test of ln w in §2.4)
  *   jk_direct, jk_lognormal : jackknife errors (§2.1): the unbiased spread of the
  *                         n_sub subset estimates (each with its own n_total) / sqrt(n_sub)
+ *   bias_ln, bias_se    : the next terms of ln <w> beyond Eq. (22)'s mean + var/2,
+ *                         ln <w> = k1 + k2/2 + k3/6 + k4/24 + ... (cumulants of ln w),
+ *                         estimated by the unbiased k-statistics of ln w in the bin as
+ *                         k3/6 + k4/24, and its standard error under normality
+ *                         sqrt(var k3 / 36 + var k4 / 576), var k3 = 6 n k2^3/((n-1)(n-2)),
+ *                         var k4 = 24 n (n+1) k2^4/((n-1)(n-2)(n-3)).  p_lognormal
+ *                         exp(bias_ln) is the cumulant-corrected estimate; a skewness
+ *                         of ln w too small for the normality test still shifts the
+ *                         lognormal estimate by about bias_ln.
  * Empty bin: both estimates 0, eps 0.  The lognormal estimate needs n_j >= 2,
- * the normality test n_j >= 8 and var_lw > 0, the jackknife n_sub >= 2 and
- * every subset's estimate defined; otherwise NaN.  128 bytes. */
+ * the bias terms n_j >= 4, the normality test n_j >= 8 (both var_lw > 0), the
+ * jackknife n_sub >= 2 and every subset's estimate defined; otherwise NaN.
+ * 144 bytes. */
 typedef struct fpt_estimate_bin {
     double count, p_direct, se_direct, p_lognormal, eps_lo, eps_hi, mean_lw, var_lw;
     double skew, kurt, z_skew, z_kurt, k2, p_normal, jk_direct, jk_lognormal;
+    double bias_ln, bias_se;
 } fpt_estimate_bin;
 
 /* Estimates of one histogram made by fpt_histogram (or one set's histogram of
@@ -339,7 +367,7 @@ int fpt_mlp_backward(const fpt_mlp_params* w, const float* phi, const float* N, 
                      float* grad, void* stream);
 
 /* Autotuner of the stepper's launch shape (threads per block in {128, 256, 512}
- * and steps per scheduling block k_steps in {8, 16, 32, 64}, binary64: {4, 8};
+ * and steps per scheduling block k_steps in {16, 32, 64}, binary64: {4, 8};
  * the binary32 power-law bias kernels exist for 32 only).
  * Runs pilot launches over the given sets with each n_traj scaled by
  * `fraction` in (0, 1] (raised if needed so the pilot fills the GPU), times
@@ -371,17 +399,22 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
  * latency-bound loop that cannot afford an allocation failing mid-run or the
  * device synchronisation that freeing memory implies.  The caller passes the
  * inputs (host sets array) and the device outputs exactly as for
- * fpt_simulate_batch; the stepper's scratch (ticket counter, step total, status
- * word and up to FPT_NOALLOC_MAX_SETS per-set constant blocks, under 8 KB) is a
- * fixed array inside the library that every GPU loading the library keeps
- * until the process exits.  No device memory is allocated or freed.
+ * fpt_simulate_batch; the stepper's scratch (ticket counter, step total and
+ * status word in a 256-byte header, then up to FPT_NOALLOC_MAX_SETS per-set
+ * constant blocks: 15,232 bytes in all) is a fixed array inside the library
+ * that every GPU loading the library keeps until the process exits.  No device
+ * memory is allocated or freed.
  *   - n_sets must be in [1, FPT_NOALLOC_MAX_SETS]; more is rejected with
  *     FPT_EINVAL (fpt_last_error() says why).
- *   - The first call on a device looks up the array's device address for that
- *     device (and caches it); make that first call before any stream capture.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     with that device current and caches it (again for a new CUDA context on
+ *     the same device); make that first call before any stream capture.
  *   - All calls share the one array: each call re-initialises what it uses,
  *     but calls whose GPU work overlaps (other streams or host threads) race
  *     on it and must be serialised by the caller.
+ *   - The call uploads the scratch image from host memory, launches the
+ *     stepper and reads the status word back: it synchronises `stream`
+ *     before returning.
  *   - Results equal those of fpt_simulate_batch with the same arguments. */
 #define FPT_NOALLOC_MAX_SETS 48
 int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* sets, int32_t n_sets,
@@ -391,8 +424,9 @@ int fpt_simulate_batch_noalloc(const fpt_params* p, const fpt_set* sets, int32_t
  * of run `traj` of set `set_id` (exactly what the stepper draws; §2.1 below
  * Eq. (8)), written to the device array out as double (FPT_PREC_F64) or float
  * (the binary32 precisions), 4 * n_blocks values.  precision =
- * FPT_NORMALS_RAW_BITS writes the 4 Philox words of each block as uint32
- * instead.  Synchronises `stream`. */
+ * FPT_NORMALS_RAW_BITS writes instead the 4 Philox words of each counter
+ * c = k0 .. k0 + n_blocks - 1 (counter (c, traj_lo, traj_hi, set_id)) as
+ * uint32.  Synchronises `stream`. */
 #define FPT_NORMALS_RAW_BITS 3
 int fpt_normals(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k0, int64_t n_blocks,
                 int32_t precision, void* out, void* stream);
@@ -407,6 +441,40 @@ int fpt_normals(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k0, int6
  * kernel's duration in seconds to *seconds_out (may be NULL).  The context
  * stays usable.  Synchronises `stream`. */
 int fpt_wait_selftest(int32_t* expired_out, double* seconds_out, void* stream);
+
+/* Failure injection on the host (no paper counterpart; for tests of the error
+ * paths without faulting a GPU).
+ * fpt_inject_alloc_failures(count): the next `count` device allocations of
+ * the library's scratch (any entry point) fail as if the device were full:
+ * no memory is requested, the call returns FPT_ENOMEM, and later calls run
+ * normally.  count = 0 cancels pending failures; count < 0 is FPT_EINVAL.
+ * fpt_inject_status(bits): the next fpt_simulate, fpt_simulate_batch or
+ * fpt_simulate_batch_host call starts its device status word at `bits`
+ * instead of 0; the kernels run normally and the call returns
+ * FPT_EDEVICE_STATUS when bits != 0 (the path a device-side check takes).
+ * Both settings are process-wide. */
+int fpt_inject_alloc_failures(int32_t count);
+int fpt_inject_status(uint32_t bits);
+
+/* Measured throughput of the execution pipes the kernels are bound by, on the
+ * current device (no paper counterpart: the denominators of the kernels'
+ * rooflines).  Each figure is thread operations per second of a loop of one
+ * instruction kind over independent dependency chains on every SM (32 warps
+ * per SM), timed with CUDA events after a warm-up launch, at the clock the GPU
+ * runs at during the call:
+ *   fp64_fma_per_s   binary64 fused multiply-adds (the FP64 pipe),
+ *   xu_lg2_per_s     lg2.approx.f32 (the XU / MUFU pipe),
+ *   wide_mul_per_s   mul.wide.u32, the 32 x 32 -> 64-bit multiply of a
+ *                    Philox round (the fma-heavy pipe),
+ *   fp32_fma_per_s   binary32 fused multiply-adds.
+ * Takes about 0.1 s; synchronises `stream`. */
+typedef struct {
+    double fp64_fma_per_s;
+    double xu_lg2_per_s;
+    double wide_mul_per_s;
+    double fp32_fma_per_s;
+} fpt_pipe_rates_out;
+int fpt_pipe_rates(fpt_pipe_rates_out* out, void* stream);
 
 /* Human-readable name of a return code (static string). */
 const char* fpt_strerror(int code);

@@ -17,6 +17,13 @@ Per bin j = (lo + j d, lo + (j+1) d] (right-closed, §2.1 Eq. (9)):
     the skewness transform of D'Agostino (1970) and the kurtosis transform of
     Anscombe and Glynn (1983), as combined by D'Agostino, Belanger and
     D'Agostino (1990);
+  * the lognormal estimate's next terms (reading of §2.4 Eq. (22)): ln <w> =
+    k1 + k2/2 + k3/6 + k4/24 + ... in the cumulants of ln w; Eq. (22) keeps the
+    first two, so bias_ln = k3/6 + k4/24 with the unbiased k-statistics k3, k4
+    of ln w in the bin, and bias_se its standard error under normality,
+    sqrt(var(k3)/36 + var(k4)/576), var(k3) = 6 n k2^3 / ((n-1)(n-2)),
+    var(k4) = 24 n (n+1) k2^4 / ((n-1)(n-2)(n-3)) (Fisher's k-statistics;
+    needs n_j >= 4 and s^2 > 0, NaN otherwise);
   * jackknife (§2.1): run i belongs to subset (id_offset + i) mod n_sub; each
     subset's estimate uses its own n_total; the spread of the n_sub estimates
     (unbiased variance) scaled from n_total / n_sub runs to n_total by the
@@ -28,7 +35,9 @@ the normality test needs n_j >= 8 and s^2 > 0 (NaN otherwise); the jackknife
 needs n_sub >= 2 and every subset's estimate defined (NaN otherwise).
 
 Parity status: pinned (tests/test_oracle_estimate.py) by scipy.stats.normaltest,
-skewtest and kurtosistest on the same samples; by the lognormal mean and the
+skewtest and kurtosistest on the same samples; the k-statistics by
+scipy.stats.kstat and their variances by simulation of normal samples; the
+bias terms by ln w with a gamma-shaped skew, whose <w> is known in closed form; by the lognormal mean and the
 coverage of eps on exactly lognormal weights; by the reduction of Eq. (16) and
 Eq. (23) to Eq. (9) when w = 1; by a hand-computed jackknife example.
 """
@@ -37,7 +46,7 @@ import math
 import numpy as np
 
 FIELDS = ("count", "p_direct", "se_direct", "p_lognormal", "eps_lo", "eps_hi", "mean_lw", "var_lw",
-          "skew", "kurt", "z_skew", "z_kurt", "k2", "p_normal", "jk_direct", "jk_lognormal")
+          "skew", "kurt", "z_skew", "z_kurt", "k2", "p_normal", "jk_direct", "jk_lognormal", "bias_ln", "bias_se")
 
 
 def bin_index(N, n_bins, lo, hi):
@@ -125,6 +134,25 @@ def subset_totals(n, n_sub, id_offset):
     return np.bincount(k.astype(np.int64), minlength=n_sub)
 
 
+def lognormal_bias(x):
+    """(k3/6 + k4/24, its standard error) from the unbiased k-statistics of the
+    sample x (NaN for fewer than 4 values or zero variance)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    if n < 4:
+        return math.nan, math.nan
+    c = x - x.mean()
+    m2, m3, m4 = np.mean(c ** 2), np.mean(c ** 3), np.mean(c ** 4)
+    if not m2 > 0:
+        return math.nan, math.nan
+    k2 = n / (n - 1) * m2
+    k3 = n * n / ((n - 1) * (n - 2)) * m3
+    k4 = n * n * ((n + 1) * m4 - 3 * (n - 1) * m2 * m2) / ((n - 1) * (n - 2) * (n - 3))
+    v3 = 6 * n * k2 ** 3 / ((n - 1) * (n - 2))
+    v4 = 24 * n * (n + 1) * k2 ** 4 / ((n - 1) * (n - 2) * (n - 3))
+    return k3 / 6 + k4 / 24, math.sqrt(v3 / 36 + v4 / 576)
+
+
 def estimate(N, logw, n_bins, lo, hi, n_sub=1, id_offset=0):
     """Per-bin estimators of the records (N_i, ln w_i), i = 0 .. n-1 (run ids
     id_offset + i).  Returns a dict of float64 arrays [n_bins], keys FIELDS."""
@@ -147,6 +175,7 @@ def estimate(N, logw, n_bins, lo, hi, n_sub=1, id_offset=0):
         out["p_direct"][b], out["se_direct"][b] = _direct(x, n, d)
         (out["p_lognormal"][b], out["eps_lo"][b], out["eps_hi"][b],
          out["mean_lw"][b], out["var_lw"][b]) = _lognormal(x, n, d)
+        out["bias_ln"][b], out["bias_se"][b] = lognormal_bias(x)
         if x.size >= 8 and out["var_lw"][b] > 0.0:
             (out["skew"][b], out["kurt"][b], out["z_skew"][b], out["z_kurt"][b],
              out["k2"][b], out["p_normal"][b]) = dagostino_pearson(x)

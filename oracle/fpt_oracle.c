@@ -53,22 +53,41 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 
 /* Box–Muller: two uniforms in (0, 1) give two independent unit normals,
  * r = sqrt(-2 ln u0), (r cos 2 pi u1, r sin 2 pi u1).  A 32-bit word w maps
- * to u = (w + 1/2) 2^-32, which is exact in binary64 and never 0 or 1. */
+ * to u = (w + 1/2) 2^-32 and a 16-bit field h to u = (h + 1/2) 2^-16; both are
+ * exact in binary64 and never 0 or 1. */
 static double uniform_open(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+static double uniform_open16(uint32_t h) { return ((double)h + 0.5) * 0x1p-16; }
 
+/* Which Philox words feed which normals (the paper names no generator, §2.1
+ * below Eq. (8); this assignment is a choice of the project, made the same way
+ * on both sides).  Steps come in groups of sixteen: group G = k div 4 uses the
+ * twelve words of the Philox counters (3G, id_lo, id_hi, set_id),
+ * (3G + 1, ...), (3G + 2, ...), taken in that order.  The four steps of block
+ * k (steps 4k .. 4k+3) use words 3j, 3j + 1 and 3j + 2 of the twelve, with
+ * j = k mod 4: the first two are the radius words of the block's two
+ * Box–Muller pairs, the third holds their angles, the first pair's in its
+ * high 16 bits and the second pair's in its low 16 bits.  A pair thus takes
+ * 48 bits.  Angles at the 2^16 midpoints of equal arcs reproduce every
+ * trigonometric moment of degree below 2^16 exactly, so the normals keep
+ * their law; the radius keeps all 32 bits. */
 void oracle_normals4(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k, double xi[4]) {
-    const uint32_t ctr[4] = {k, (uint32_t)traj, (uint32_t)(traj >> 32), set_id};
+    const uint32_t G = k / 4, j = k % 4;
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t w[4];
-    oracle_philox4x32_10(ctr, key, w);
+    uint32_t words[12];
+    for (uint32_t c = 0; c < 3; ++c) {
+        const uint32_t ctr[4] = {3 * G + c, (uint32_t)traj, (uint32_t)(traj >> 32), set_id};
+        oracle_philox4x32_10(ctr, key, words + 4 * c);
+    }
+    const uint32_t radius[2] = {words[3 * j], words[3 * j + 1]};
+    const uint32_t angle[2] = {words[3 * j + 2] >> 16, words[3 * j + 2] & 0xFFFFu};
     const double two_pi = 6.283185307179586; /* 2 pi rounded to binary64 */
     for (int p = 0; p < 2; ++p) {
-        double u0 = uniform_open(w[2 * p]);
-        double u1 = uniform_open(w[2 * p + 1]);
+        double u0 = uniform_open(radius[p]);
+        double u1 = uniform_open16(angle[p]);
         double r = sqrt(-2.0 * log(u0));
-        double angle = two_pi * u1;
-        xi[2 * p] = r * cos(angle);
-        xi[2 * p + 1] = r * sin(angle);
+        double a = two_pi * u1;
+        xi[2 * p] = r * cos(a);
+        xi[2 * p + 1] = r * sin(a);
     }
 }
 

@@ -62,8 +62,10 @@ typedef struct {
 /* Philox4x32-10 block function: out = Philox(ctr, key), 10 rounds. */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-/* The four standard normals used by steps 4k .. 4k+3 of trajectory `traj`
- * (Box–Muller on one Philox block with counter (k, traj_lo, traj_hi, set_id)). */
+/* The four standard normals used by steps 4k .. 4k+3 of trajectory `traj`:
+ * Box–Muller on three of the twelve words of the Philox counters
+ * (3G + c, traj_lo, traj_hi, set_id), c = 0, 1, 2, G = k div 4 (the word
+ * assignment is spelled out in fpt_oracle.c). */
 void oracle_normals4(uint64_t seed, uint64_t traj, uint32_t set_id, uint32_t k, double xi[4]);
 
 /* Simulate n runs with global ids traj_offset + i.  Writes the first-passage

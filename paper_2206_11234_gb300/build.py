@@ -4,6 +4,13 @@ Each translation unit is compiled by nvcc in parallel, then linked into
 paper_2206_11234_gb300/libfpt_gb300.so.  The binary64 stepper and the RNG
 probe are compiled with FMA contraction off so that their arithmetic is
 rounded exactly as written in the source.
+
+build(debug=True) builds the same sources with -DFPT_DEBUG=1 into
+libfpt_gb300_debug.so: kernels whose bounds checks (parameter set of a
+ticket, replay-queue capacity, record index, histogram bin index) record a
+status bit and skip the access, reported by the call as FPT_EDEVICE_STATUS.
+The binding loads it instead of the default library when the environment
+variable FPT_DEBUG_LIB is 1.
 """
 import concurrent.futures as cf
 import os
@@ -34,6 +41,8 @@ UNITS = {
     "train.cu": [],
     "plan.cu": [],
     "estimate.cu": [],
+    "pipes.cu": [],
+    "hist_merge.cu": [],
 }
 
 
@@ -51,22 +60,33 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+LIB_DEBUG = os.path.join(HERE, "libfpt_gb300_debug.so")
+
+
+def lib_path(debug: bool = False) -> str:
+    return LIB_DEBUG if debug else LIB
+
+
+def up_to_date(debug: bool = False) -> bool:
+    lib = lib_path(debug)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = lib_path(debug)
+    if not force and up_to_date(debug):
+        return lib
+    build_dir = BUILD + ("_debug" if debug else "")
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
+    extra = ["-DFPT_DEBUG=1"] if debug else []
 
     def compile_unit(name):
-        obj = os.path.join(BUILD, name.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *UNITS[name], "-c", os.path.join(CSRC, name), "-o", obj]
+        obj = os.path.join(build_dir, name.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *COMMON, *extra, *UNITS[name], "-c", os.path.join(CSRC, name), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -79,14 +99,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for obj, log in results:
             print(obj, log, file=sys.stderr)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -29,6 +31,44 @@ int fail(int code, const char* fmt, ...) {
     g_last_error = buf;
     return code;
 }
+
+namespace {
+std::atomic<int> g_fail_allocs{0};
+std::atomic<unsigned> g_inject_status{0u};
+
+bool take_alloc_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+}  // namespace
+
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    if (take_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t lib_malloc_from_pool_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st) {
+    if (take_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+    if (take_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+unsigned take_injected_status() { return g_inject_status.exchange(0u); }
 
 int cuda_fail(cudaError_t e, const char* what) {
     if (e == cudaErrorMemoryAllocation) return fail(FPT_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
@@ -345,8 +385,9 @@ int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L
         int n_sm = 0;
         rc = device_sm_count(&n_sm);
         if (rc) return rc;
+        unsigned* status = reinterpret_cast<unsigned*>(ws + L.off_scratch + offsetof(StepperScratch, status));
         cudaError_t e = hist_launch(reinterpret_cast<const HistSeg*>(ws + L.off_segs), (int)P.segs.size(),
-                                    P.max_nb, P.max_n, out_N, out_logw, bins, counts, n_sm, stream);
+                                    P.max_nb, P.max_n, out_N, out_logw, bins, counts, n_sm, stream, status);
         if (e != cudaSuccess) return cuda_fail(e, "histogram launch");
     }
     return FPT_OK;
@@ -371,8 +412,11 @@ int run_once(const fpt_params* p, const Prepared& P, uint64_t seed, double* out_
     workspace_layout(P, &L);
     std::vector<unsigned char> img;
     workspace_image(P, L, &img);
+    // status bits injected by the host (fpt_inject_status) start the call's status word
+    const unsigned injected = take_injected_status();
+    std::memcpy(img.data() + L.off_scratch + offsetof(StepperScratch, status), &injected, sizeof(injected));
     unsigned char* ws = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.bytes, stream);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&ws), L.bytes, stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     // pageable source: the copy is staged before the call returns
     e = cudaMemcpyAsync(ws, img.data(), L.bytes, cudaMemcpyHostToDevice, stream);
@@ -393,6 +437,7 @@ extern "C" {
 
 int fpt_simulate(const fpt_params* p, int64_t n_traj, double phi_in, double phi_end, double phi_uv,
                  double dN, double bias, uint64_t seed, double* out_N, double* out_logw) {
+    NvtxRange nvtx_range("fpt_simulate");
     int rc = check_params(p);
     if (rc) return rc;
     if (n_traj < 0) return fail(FPT_EINVAL, "n_traj %lld < 0", (long long)n_traj);
@@ -418,6 +463,7 @@ int fpt_simulate(const fpt_params* p, int64_t n_traj, double phi_in, double phi_
 
 int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                        double* out_N, double* out_logw, fpt_bin* out_bins, fpt_hist_counts* out_counts) {
+    NvtxRange nvtx_range("fpt_simulate_batch");
     int rc = check_params(p);
     if (rc) return rc;
     if ((out_bins == nullptr) != (out_counts == nullptr))
@@ -431,6 +477,7 @@ int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets,
 
 int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo, double hi,
                   int32_t n_sub, uint64_t id_offset, fpt_bin* bins, fpt_hist_counts* counts, void* stream) {
+    NvtxRange nvtx_range("fpt_histogram");
     if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);
     int rc = check_hist(n_bins, lo, hi, n_sub);
     if (rc) return rc;
@@ -446,23 +493,35 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
     h.n_bins = n_bins;
     h.n_sub = n_sub;
     h.bin0 = 0;
-    HistSeg* d_seg = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_seg), sizeof(HistSeg), st);
+    // workspace: the segment, then the status word (zero)
+    struct HistWork {
+        HistSeg seg;
+        unsigned status;
+    } hw{};
+    hw.seg = h;
+    HistWork* d_w = nullptr;
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&d_w), sizeof(HistWork), st);
     if (e != cudaSuccess) return cuda_fail(e, "histogram workspace");
-    e = cudaMemcpyAsync(d_seg, &h, sizeof(HistSeg), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(d_w, &hw, sizeof(HistWork), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "histogram upload");
     int n_sm = 0;
     if (!rc) rc = device_sm_count(&n_sm);
     if (!rc) {
-        e = hist_launch(d_seg, 1, n_bins * n_sub, n, N, logw, bins, counts, n_sm, st);
+        e = hist_launch(&d_w->seg, 1, n_bins * n_sub, n, N, logw, bins, counts, n_sm, st, &d_w->status);
         if (e != cudaSuccess) rc = cuda_fail(e, "histogram launch");
     }
-    cudaError_t ef = cudaFreeAsync(d_seg, st);
+    unsigned status = 0u;
+    if (!rc) {
+        e = cudaMemcpyAsync(&status, &d_w->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "status readback");
+    }
+    cudaError_t ef = cudaFreeAsync(d_w, st);
     if (!rc) {
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "stream synchronize");
     }
     if (!rc && ef != cudaSuccess) rc = cuda_fail(ef, "histogram workspace free");
+    if (!rc && status != 0u) rc = fail(FPT_EDEVICE_STATUS, "device status 0x%x", status);
     return rc;
 }
 
@@ -506,6 +565,7 @@ cudaError_t host_entry_pool(cudaMemPool_t* out) {
 int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                             double* host_N, double* host_logw, fpt_bin* host_bins,
                             fpt_hist_counts* host_counts) {
+    NvtxRange nvtx_range("fpt_simulate_batch_host");
     int rc = check_params(p);
     if (rc) return rc;
     if (!host_bins || !host_counts) return fail(FPT_EINVAL, "host_bins and host_counts are required");
@@ -524,7 +584,7 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
     cudaMemPool_t pool;
     cudaError_t e = host_entry_pool(&pool);
     if (e != cudaSuccess) return cuda_fail(e, "memory pool");
-    e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dev), total, pool, st);
+    e = lib_malloc_from_pool_async(reinterpret_cast<void**>(&dev), total, pool, st);
     if (e != cudaSuccess) return cuda_fail(e, "device buffers");
     double* dN_ = reinterpret_cast<double*>(dev + o_N);
     double* dlw = reinterpret_cast<double*>(dev + o_lw);
@@ -569,5 +629,16 @@ const char* fpt_strerror(int code) {
 const char* fpt_last_error(void) { return g_last_error.c_str(); }
 
 int fpt_abi_version(void) { return FPT_ABI_VERSION; }
+
+int fpt_inject_alloc_failures(int32_t count) {
+    if (count < 0) return fail(FPT_EINVAL, "count %d < 0", count);
+    g_fail_allocs.store(count);
+    return FPT_OK;
+}
+
+int fpt_inject_status(uint32_t bits) {
+    g_inject_status.store(bits);
+    return FPT_OK;
+}
 
 }  // extern "C"

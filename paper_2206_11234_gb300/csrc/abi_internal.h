@@ -1,6 +1,7 @@
 // Internal helpers shared by the C ABI translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -9,6 +10,24 @@
 #include "stepper_launch.h"
 
 namespace fpt {
+
+// Device allocations of the library's scratch.  While failures are pending
+// (fpt_inject_alloc_failures) each call consumes one and returns
+// cudaErrorMemoryAllocation without allocating, as a full device would.
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st);
+cudaError_t lib_malloc_from_pool_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st);
+cudaError_t lib_malloc(void** p, size_t bytes);
+// Status bits to pre-set in the next uploaded stepper scratch (fpt_inject_status), consumed.
+unsigned take_injected_status();
+
+// NVTX range over one entry point (shows the library's calls on a profiler's
+// timeline; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Record a failure message for fpt_last_error() and return `code`.
 int fail(int code, const char* fmt, ...);

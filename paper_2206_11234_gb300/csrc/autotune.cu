@@ -48,6 +48,7 @@ using namespace fpt;
 extern "C" int fpt_autotune(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                             double fraction, int32_t* block_dim_out, int32_t* k_steps_out,
                             double* steps_per_s_out) {
+    NvtxRange nvtx_range("fpt_autotune");
     int rc = check_params(p);
     if (rc) return rc;
     if (!sets) return fail(FPT_EINVAL, "sets is NULL");
@@ -77,7 +78,7 @@ extern "C" int fpt_autotune(const fpt_params* p, const fpt_set* sets, int32_t n_
     workspace_image(P, L, &img);
     const size_t rec_bytes = (size_t)P.n_total * sizeof(double);
     unsigned char* dev = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), L.bytes + 2 * rec_bytes + 512, st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&dev), L.bytes + 2 * rec_bytes + 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "autotune buffers");
     unsigned char* ws = dev;
     double* outN = reinterpret_cast<double*>(dev + (L.bytes + 255) / 256 * 256);
@@ -87,12 +88,12 @@ extern "C" int fpt_autotune(const fpt_params* p, const fpt_set* sets, int32_t n_
     cudaEventCreate(&e1);
 
     const int blocks[3] = {128, 256, 512};
-    const int ks32[4] = {8, 16, 32, 64};  // binary32 block lengths
+    const int ks32[3] = {16, 32, 64};     // binary32 block lengths (whole 16-step groups)
     const int ks64[2] = {4, 8};           // binary64
     const int ks_pow[1] = {32};          // binary32 power-law bias kernels
     const bool pw = p->bias_kind == FPT_BIAS_POWER && p->precision != FPT_PREC_F64;
     const int* kss = p->precision == FPT_PREC_F64 ? ks64 : (pw ? ks_pow : ks32);
-    const int nks = p->precision == FPT_PREC_F64 ? 2 : (pw ? 1 : 4);
+    const int nks = p->precision == FPT_PREC_F64 ? 2 : (pw ? 1 : 3);
     double best = -1.0;
     int best_b = 256, best_k = kss[0];
     fpt_params q = *p;

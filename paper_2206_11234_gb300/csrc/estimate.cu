@@ -178,6 +178,24 @@ __global__ void estimate_kernel(const fpt_bin* __restrict__ bins, int n_bins, in
             o.p_normal = exp(-0.5 * o.k2);
         }
     }
+    // ---- the next cumulant terms of ln <w>: k3/6 + k4/24 (k-statistics) ----
+    o.bias_ln = o.bias_se = qnan;
+    if (A.n >= 4.0 && o.var_lw > 0.0) {
+        const double n = A.n;
+        const double a1 = A.l[1] / n, a2 = A.l[2] / n, a3 = A.l[3] / n, a4 = A.l[4] / n;
+        const double m2 = a2 - a1 * a1;
+        const double m3 = a3 - 3.0 * a1 * a2 + 2.0 * a1 * a1 * a1;
+        const double m4 = a4 - 4.0 * a1 * a3 + 6.0 * a1 * a1 * a2 - 3.0 * a1 * a1 * a1 * a1;
+        if (m2 > 0.0) {
+            const double k2 = n / (n - 1.0) * m2;
+            const double k3 = n * n / ((n - 1.0) * (n - 2.0)) * m3;
+            const double k4 = n * n * ((n + 1.0) * m4 - 3.0 * (n - 1.0) * m2 * m2) / ((n - 1.0) * (n - 2.0) * (n - 3.0));
+            const double v3 = 6.0 * n * k2 * k2 * k2 / ((n - 1.0) * (n - 2.0));
+            const double v4 = 24.0 * n * (n + 1.0) * k2 * k2 * k2 * k2 / ((n - 1.0) * (n - 2.0) * (n - 3.0));
+            o.bias_ln = k3 / 6.0 + k4 / 24.0;
+            o.bias_se = sqrt(v3 / 36.0 + v4 / 576.0);
+        }
+    }
     // ---- jackknife over the subsets (§2.1) ----
     o.jk_direct = o.jk_lognormal = qnan;
     if (n_sub >= 2) {
@@ -338,6 +356,7 @@ using namespace fpt;
 
 extern "C" int fpt_stitch(const fpt_estimate_bin* est, int32_t n_runs, int32_t n_bins, int32_t estimator,
                           int64_t min_count, double p_threshold, fpt_stitch_bin* out, void* stream) {
+    NvtxRange nvtx_range("fpt_stitch");
     if (!est || !out) return fail(FPT_EINVAL, "pointer is NULL");
     if (n_runs < 1 || n_bins < 1) return fail(FPT_EINVAL, "n_runs %d and n_bins %d must be >= 1", n_runs, n_bins);
     if (estimator != FPT_ESTIMATOR_DIRECT && estimator != FPT_ESTIMATOR_LOGNORMAL)
@@ -354,6 +373,7 @@ extern "C" int fpt_stitch(const fpt_estimate_bin* est, int32_t n_runs, int32_t n
 }
 
 extern "C" int fpt_pearson(const double* N, const double* logw, int64_t n, double* out, void* stream) {
+    NvtxRange nvtx_range("fpt_pearson");
     if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);
     if (!out || (n > 0 && (!N || !logw))) return fail(FPT_EINVAL, "pointer is NULL");
     int n_sm = 0;
@@ -377,6 +397,7 @@ extern "C" int fpt_pearson(const double* N, const double* logw, int64_t n, doubl
 
 extern "C" int fpt_estimate(const fpt_bin* bins, int32_t n_bins, int32_t n_sub, double lo, double hi,
                             int64_t n_total, uint64_t id_offset, fpt_estimate_bin* out, void* stream) {
+    NvtxRange nvtx_range("fpt_estimate");
     if (!bins || !out) return fail(FPT_EINVAL, "pointer is NULL");
     if (n_bins < 1 || n_sub < 1 || (int64_t)n_bins * n_sub > FPT_MAX_HIST_BINS)
         return fail(FPT_EINVAL, "n_bins %d x n_sub %d not in [1, %d]", n_bins, n_sub, FPT_MAX_HIST_BINS);

@@ -34,11 +34,18 @@ constexpr unsigned long long kKeyNegInf = 0x000fffffffffffffull;  // ord_key(-in
 constexpr int kSums = 6;  // s1, s2, l1 .. l4 per bin
 
 // 0: in range (bin set), 1: N <= lo, 2: finite N > hi, 3: N not finite
-__device__ __forceinline__ int classify(double N, const HistSeg& h, unsigned long long gid, int& bin) {
+__device__ __forceinline__ int classify(double N, const HistSeg& h, unsigned long long gid, int& bin,
+                                        unsigned* status) {
     if (!(N < __longlong_as_double(0x7ff0000000000000ll))) return 3;
     if (N <= h.lo) return 1;
     if (N > h.hi) return 2;
     long long j = (long long)ceil((N - h.lo) / h.d) - 1;
+#if FPT_DEBUG
+    // rounding at the edges gives -1 or n_bins, which the clamp absorbs; more is a broken segment
+    if ((j < -1 || j > h.n_bins) && status) atomicOr(status, kStatusHistBin);
+#else
+    (void)status;
+#endif
     if (j < 0) j = 0;
     if (j > h.n_bins - 1) j = h.n_bins - 1;
     const int sub = (int)(gid % (unsigned long long)h.n_sub);
@@ -71,7 +78,7 @@ __global__ void hist_init(const HistSeg* __restrict__ segs, int n_segs, fpt_bin*
 
 __global__ void hist_pass_max(const double* __restrict__ N, const double* __restrict__ lw,
                               const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins,
-                              fpt_hist_counts* __restrict__ counts) {
+                              fpt_hist_counts* __restrict__ counts, unsigned* status) {
     extern __shared__ unsigned long long s_key[];
     const HistSeg h = segs[blockIdx.y];
     const int nb = h.n_bins * h.n_sub;
@@ -88,7 +95,7 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
         unsigned long long key = 0;
         if (i < h.n) {
             const long long r = h.first + i;
-            const int cat = classify(N[r], h, h.id_offset + (unsigned long long)i, bin);
+            const int cat = classify(N[r], h, h.id_offset + (unsigned long long)i, bin, status);
             under += (cat == 1);
             over += (cat == 2);
             cens += (cat == 3);
@@ -126,7 +133,7 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
 }
 
 __global__ void hist_pass_sum(const double* __restrict__ N, const double* __restrict__ lw,
-                              const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins) {
+                              const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins, unsigned* status) {
     extern __shared__ double s_acc[];  // [nb][kSums] sums, then [nb] counts
     const HistSeg h = segs[blockIdx.y];
     const int nb = h.n_bins * h.n_sub;
@@ -143,7 +150,7 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
         double v[kSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (i < h.n) {
             const long long r = h.first + i;
-            if (classify(N[r], h, h.id_offset + (unsigned long long)i, bin) == 0) {
+            if (classify(N[r], h, h.id_offset + (unsigned long long)i, bin, status) == 0) {
                 const unsigned long long k =
                     (unsigned long long)__double_as_longlong(bins[h.bin0 + bin].max_lw);
                 const double x = lw[r] - ord_value(k);
@@ -208,7 +215,7 @@ size_t hist_smem_bytes(int max_nb) { return (size_t)max_nb * (kSums * sizeof(dou
 
 cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long max_n,
                         const double* N, const double* lw, fpt_bin* bins, fpt_hist_counts* counts,
-                        int n_sm, cudaStream_t stream) {
+                        int n_sm, cudaStream_t stream, unsigned* status) {
     const size_t smem_sum = hist_smem_bytes(max_nb);
     const size_t smem_max = (size_t)max_nb * sizeof(unsigned long long);
     // opt in to large dynamic shared memory (per device; cheap to repeat)
@@ -228,10 +235,10 @@ cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long
     int per_seg = (int)(want < 1 ? 1 : want);
     const int cap = (2 * n_sm + n_segs - 1) / n_segs;
     if (per_seg > cap) per_seg = cap < 1 ? 1 : cap;
-    hist_pass_max<<<dim3(per_seg, n_segs), threads, smem_max, stream>>>(N, lw, d_segs, bins, counts);
+    hist_pass_max<<<dim3(per_seg, n_segs), threads, smem_max, stream>>>(N, lw, d_segs, bins, counts, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    hist_pass_sum<<<dim3(per_seg, n_segs), threads, smem_sum, stream>>>(N, lw, d_segs, bins);
+    hist_pass_sum<<<dim3(per_seg, n_segs), threads, smem_sum, stream>>>(N, lw, d_segs, bins, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     hist_final<<<dim3(init_blocks, n_segs), threads, 0, stream>>>(d_segs, bins);

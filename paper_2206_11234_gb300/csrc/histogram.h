@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "fpt.h"
+#include "status.h"
 
 namespace fpt {
 
@@ -20,8 +21,9 @@ size_t hist_smem_bytes(int max_nb);
 
 // Enqueue the four histogram kernels for n_segs segments (device array
 // d_segs).  max_nb = max over segments of n_bins * n_sub, max_n = max records.
+// status: device status word (nullable), written only by FPT_DEBUG checks.
 cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long max_n,
                         const double* N, const double* lw, fpt_bin* bins, fpt_hist_counts* counts,
-                        int n_sm, cudaStream_t stream);
+                        int n_sm, cudaStream_t stream, unsigned* status);
 
 }  // namespace fpt

@@ -296,7 +296,7 @@ extern "C" int fpt_wait_selftest(int32_t* expired_out, double* seconds_out, void
     if (!expired_out) return fail(FPT_EINVAL, "expired_out is NULL");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned* d = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(unsigned), st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&d), sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e, "self-test flag");
     cudaMemsetAsync(d, 0, sizeof(unsigned), st);
     cudaEvent_t a, b;
@@ -322,6 +322,7 @@ extern "C" int fpt_wait_selftest(int32_t* expired_out, double* seconds_out, void
 
 extern "C" int fpt_mlp_forward(const fpt_mlp_params* w, const float* phi, const float* N, int64_t n, float* out_b,
                                void* stream) {
+    NvtxRange nvtx_range("fpt_mlp_forward");
     if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);
     if (!w || (n > 0 && (!phi || !N || !out_b))) return fail(FPT_EINVAL, "pointer is NULL");
     if ((reinterpret_cast<uintptr_t>(w) & 15u) != 0) return fail(FPT_EINVAL, "parameters must be 16-byte aligned");
@@ -332,7 +333,7 @@ extern "C" int fpt_mlp_forward(const fpt_mlp_params* w, const float* phi, const 
     int rc = mlp_grid((const void*)mlp_forward_kernel, smem, kFwdTmemCols, (n + 127) / 128, &grid);
     if (rc) return rc;
     unsigned* d_status = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_status), sizeof(unsigned), st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&d_status), sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e, "MLP status");
     cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
     mlp_forward_kernel<<<grid, 128, smem, st>>>(w, phi, N, (long long)n, out_b, d_status);
@@ -346,6 +347,7 @@ extern "C" int fpt_mlp_forward(const fpt_mlp_params* w, const float* phi, const 
 
 extern "C" int fpt_mlp_backward(const fpt_mlp_params* w, const float* phi, const float* N, const float* g,
                                 int64_t n, float* grad, void* stream) {
+    NvtxRange nvtx_range("fpt_mlp_backward");
     if (n < 0) return fail(FPT_EINVAL, "n %lld < 0", (long long)n);
     if (!w || !grad || (n > 0 && (!phi || !N || !g))) return fail(FPT_EINVAL, "pointer is NULL");
     if ((reinterpret_cast<uintptr_t>(w) & 15u) != 0) return fail(FPT_EINVAL, "parameters must be 16-byte aligned");
@@ -356,7 +358,7 @@ extern "C" int fpt_mlp_backward(const fpt_mlp_params* w, const float* phi, const
     int rc = mlp_grid((const void*)mlp_backward_kernel, smem, kBwdTmemCols, (n + 127) / 128, &grid);
     if (rc) return rc;
     unsigned* d_status = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_status), sizeof(unsigned), st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&d_status), sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e, "MLP status");
     cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
     mlp_backward_kernel<<<grid, 128, smem, st>>>(w, phi, N, g, (long long)n, grad, d_status);

@@ -6,8 +6,9 @@
 // own pool allocator or a fixed memory budget, or a latency-bound loop that
 // cannot accept an allocation failing half-way through a run or the implicit
 // device synchronisation of releasing memory.  They pass their own output
-// buffers; the few hundred bytes of scratch the stepper needs (ticket counter,
-// step total, status word and the per-set constants) live in g_noalloc_scratch.
+// buffers; the scratch the stepper needs (ticket counter, step total and
+// status word in a 256-byte header, then the per-set constants of up to
+// FPT_NOALLOC_MAX_SETS sets: 15,232 bytes in all) lives in g_noalloc_scratch.
 //
 // The array is part of the library image: every GPU that loads the library
 // holds it until the process exits.  All calls share it and it keeps the last
@@ -15,6 +16,7 @@
 // counters, fresh per-set constants) before launching.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // it and must be serialised by the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,29 +33,65 @@ namespace {
 constexpr size_t kScratchHeader = 256;  // StepperScratch, padded to the set table's alignment
 constexpr size_t kNoAllocBytes = kScratchHeader + FPT_NOALLOC_MAX_SETS * sizeof(SetConst);
 static_assert(sizeof(StepperScratch) <= kScratchHeader, "scratch header");
-static_assert(kNoAllocBytes <= 16384, "the no-alloc scratch stays modest");
+static_assert(kNoAllocBytes == 15232, "the size stated in fpt.h (FPT_NOALLOC_MAX_SETS) is out of date");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// Identity of the calling thread's current CUDA context, through the driver
+// entry points the runtime hands out (no link-time dependency on the driver
+// library); 0 when it cannot be determined.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+struct CachedAddress {
+    unsigned long long context;  // context the address belongs to
+    void* addr;
+};
 std::mutex g_addr_mu;
-void* g_addr[64] = {nullptr};
+CachedAddress g_addr[64] = {};
 
 // Device address of g_noalloc_scratch on the current device.  In host code the
-// symbol itself is only a host-side handle, so the address is looked up once
-// per device (with that device current) and cached.
+// symbol itself is only a host-side handle, so the address is looked up with
+// the device current (cudaGetSymbolAddress, which also makes sure the module is
+// loaded there) at set-up, the first call on a device, and cached.  The cache
+// is keyed on the device's current context as well, so a new context on the
+// same device (after cudaDeviceReset, or a non-primary context) repeats the
+// set-up instead of reusing an address of the old one.
 int scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(FPT_EUNSUPPORTED, "device index %d", dev);
     std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev].addr || g_addr[dev].context != current_context_id()) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // creates the device's context if needed
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_addr[dev] = p;
+        g_addr[dev] = CachedAddress{current_context_id(), p};
     }
-    *out = static_cast<unsigned char*>(g_addr[dev]);
+    *out = static_cast<unsigned char*>(g_addr[dev].addr);
     return FPT_OK;
 }
 

@@ -44,6 +44,7 @@ static void plan_free(fpt_plan* pl) {
 extern "C" int fpt_plan_create(const fpt_params* p, const fpt_set* sets, int32_t n_sets, double* out_N,
                                double* out_logw, fpt_bin* out_bins, fpt_hist_counts* out_counts,
                                fpt_plan** plan_out) {
+    NvtxRange nvtx_range("fpt_plan_create");
     if (!plan_out) return fail(FPT_EINVAL, "plan_out is NULL");
     *plan_out = nullptr;
     int rc = check_params(p);
@@ -64,7 +65,7 @@ extern "C" int fpt_plan_create(const fpt_params* p, const fpt_set* sets, int32_t
     if (!rc) {
         workspace_layout(pl->P, &pl->L);
         workspace_image(pl->P, pl->L, &img);
-        e = cudaMalloc(reinterpret_cast<void**>(&pl->ws), pl->L.bytes);
+        e = lib_malloc(reinterpret_cast<void**>(&pl->ws), pl->L.bytes);
         if (e != cudaSuccess) rc = cuda_fail(e, "plan workspace");
     }
     if (!rc) {
@@ -135,6 +136,7 @@ extern "C" int fpt_plan_create(const fpt_params* p, const fpt_set* sets, int32_t
 }
 
 extern "C" int fpt_plan_launch(fpt_plan* pl, uint64_t seed, void* stream) {
+    NvtxRange nvtx_range("fpt_plan_launch");
     if (!pl) return fail(FPT_EINVAL, "plan is NULL");
     int dev = -1;
     cudaGetDevice(&dev);

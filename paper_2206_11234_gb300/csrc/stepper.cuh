@@ -186,24 +186,27 @@ struct StepOf { using type = ModelStep<Real, MODEL>; };
 template <>
 struct StepOf<float, FPT_MODEL_QUADRATIC> { using type = QuadPsiStep; };
 
-// Four binary32 EM steps of a power model: as steps4_f32, with the block's
-// log-weight summed step by step into acc.
+// Sixteen binary32 EM steps of a power model from one Philox group: as
+// steps16_f32, with the log-weight summed step by step into acc.
 template <int MODEL, bool WALL>
-__device__ __forceinline__ void steps4_pow(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t k,
-                                           const PhiloxKeys& keys, float twouv, float& phi, float& mn,
-                                           float& acc) {
-    uint32_t w[4];
-    philox_block(pl, k, keys, w);
+__device__ __forceinline__ void steps16_pow(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t G,
+                                            const PhiloxKeys& keys, float twouv, float& phi, float& mn,
+                                            float& acc) {
+    uint32_t V[12];
+    philox_group(pl, G, keys, V);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
-        const float q = __fmul_rn(model.kq, np.rho);
-        phi = model.advance(phi, q, np.c, acc);
-        if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        const float first = phi;
-        phi = model.advance(phi, q, np.s, acc);
-        if constexpr (WALL) phi = fminf(phi, twouv - phi);
-        mn = min3f(mn, first, phi);
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const NormalPair np = group_pair_f32(V, j, p);
+            const float q = __fmul_rn(model.kq, np.rho);
+            phi = model.advance(phi, q, np.c, acc);
+            if constexpr (WALL) phi = fminf(phi, twouv - phi);
+            const float first = phi;
+            phi = model.advance(phi, q, np.s, acc);
+            if constexpr (WALL) phi = fminf(phi, twouv - phi);
+            mn = min3f(mn, first, phi);
+        }
     }
 }
 
@@ -215,24 +218,28 @@ __device__ __forceinline__ float step1_f32(const Step& model, float phi, float t
     return phi;
 }
 
-// Four binary32 EM steps from one Philox block (two Box–Muller pairs): the
-// state update, the wall, the block minimum (one three-way minimum per pair)
-// and the running sum of rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
+// Sixteen binary32 EM steps from one Philox group (three Philox blocks, eight
+// Box–Muller pairs): the state update, the wall, the block minimum (one
+// three-way minimum per pair) and the running sum of
+// rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
 template <bool WALL, typename Step>
-__device__ __forceinline__ void steps4_f32(const Step& model, const PhiloxLane& pl, uint32_t k,
-                                           const PhiloxKeys& keys, float twouv, float& phi, float& mn,
-                                           float& srho) {
-    uint32_t w[4];
-    philox_block(pl, k, keys, w);
+__device__ __forceinline__ void steps16_f32(const Step& model, const PhiloxLane& pl, uint32_t G,
+                                            const PhiloxKeys& keys, float twouv, float& phi, float& mn,
+                                            float& srho) {
+    uint32_t V[12];
+    philox_group(pl, G, keys, V);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
-        const float q = __fmul_rn(model.kq, np.rho);
-        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.c, model.tc), twouv);
-        const float first = phi;
-        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.s, model.tc), twouv);
-        mn = min3f(mn, first, phi);
-        srho = __fmaf_rn(np.rho, np.c + np.s, srho);
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const NormalPair np = group_pair_f32(V, j, p);
+            const float q = __fmul_rn(model.kq, np.rho);
+            phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.c, model.tc), twouv);
+            const float first = phi;
+            phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.s, model.tc), twouv);
+            mn = min3f(mn, first, phi);
+            srho = __fmaf_rn(np.rho, np.c + np.s, srho);
+        }
     }
 }
 
@@ -362,11 +369,6 @@ struct WSum<FPT_PREC_F64> {
 template <typename Real>
 __device__ __forceinline__ void normals4(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K, Real xi[4]);
 template <>
-__device__ __forceinline__ void normals4<float>(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
-                                                float xi[4]) {
-    normals4_f32(l, k, K, xi);
-}
-template <>
 __device__ __forceinline__ void normals4<double>(const PhiloxLane& l, uint32_t k, const PhiloxKeys& K,
                                                  double xi[4]) {
     normals4_f64(l, k, K, xi);
@@ -469,38 +471,45 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
     Real ph = e.phi0, prev = e.phi0, s2 = (Real)0;
     int M = 0;
     bool crossed = false;
-    const uint32_t k0 = (uint32_t)e.m0 >> 2;
-    for (int g = 0; g < KS / 4; ++g) {
-        if constexpr (sizeof(Real) == 4) {
-            uint32_t w[4];
-            philox_block(pl, k0 + (uint32_t)g, P.keys, w);
+    if constexpr (sizeof(Real) == 4) {
+        // binary32: whole 16-step groups, as the stepping loop draws them
+        for (int gg = 0; gg < KS / 16; ++gg) {
+            uint32_t V[12];
+            philox_group(pl, ((uint32_t)e.m0 >> 4) + (uint32_t)gg, P.keys, V);
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
-                const float q = __fmul_rn(model.kq, np.rho);
+            for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (M == 0) {
-                        const float trig = h == 0 ? np.c : np.s;
-                        prev = ph;
-                        if constexpr (is_pow_model(MODEL)) {
-                            ph = model.advance(ph, q, trig, s2);
-                        } else {
-                            ph = step1_f32<WALL>(model, ph, __fmaf_rn(q, trig, model.tc), twouv);
-                            s2 = __fmaf_rn(np.rho, trig, s2);
-                        }
-                        if constexpr (WALL && is_pow_model(MODEL)) ph = fminf(ph, twouv - ph);
-                        const int step_index = e.m0 + 4 * g + 2 * p + h;
-                        if (ph <= phi_end) {
-                            crossed = true;
-                            M = step_index + 1;
-                        } else if (step_index + 1 >= S.m_max) {
-                            M = step_index + 1;
+                for (int p = 0; p < 2; ++p) {
+                    const NormalPair np = group_pair_f32(V, j, p);
+                    const float q = __fmul_rn(model.kq, np.rho);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (M == 0) {
+                            const float trig = h == 0 ? np.c : np.s;
+                            prev = ph;
+                            if constexpr (is_pow_model(MODEL)) {
+                                ph = model.advance(ph, q, trig, s2);
+                                if constexpr (WALL) ph = fminf(ph, twouv - ph);
+                            } else {
+                                ph = step1_f32<WALL>(model, ph, __fmaf_rn(q, trig, model.tc), twouv);
+                                s2 = __fmaf_rn(np.rho, trig, s2);
+                            }
+                            const int step_index = e.m0 + 16 * gg + 4 * j + 2 * p + h;
+                            if (ph <= phi_end) {
+                                crossed = true;
+                                M = step_index + 1;
+                            } else if (step_index + 1 >= S.m_max) {
+                                M = step_index + 1;
+                            }
                         }
                     }
                 }
             }
-        } else {
+            if (__all_sync(mask, M != 0)) break;
+        }
+    } else {
+        const uint32_t k0 = (uint32_t)e.m0 >> 2;
+        for (int g = 0; g < KS / 4; ++g) {
             Real xi[4];
             normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
 #pragma unroll
@@ -523,8 +532,8 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
                     }
                 }
             }
+            if (__all_sync(mask, M != 0)) break;
         }
-        if (__all_sync(mask, M != 0)) break;
     }
     // constant bias: W is the sum of the normals (binary32 sums in rho units);
     // power models: W is ln w itself
@@ -539,6 +548,12 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
     } else {
         N = __longlong_as_double(0x7ff0000000000000ll);  // +inf: censored
     }
+#if FPT_DEBUG
+    if (e.rec >= P.n_total) {
+        atomicOr(&P.scratch->status, kStatusRecord);
+        return;
+    }
+#endif
     P.out_N[e.rec] = N;
     P.out_logw[e.rec] = is_pow_model(MODEL) ? Wtot : -S.lw_bsq * Wtot - S.lw_half_b2dN * (double)M;
     my_steps += (unsigned long long)M;
@@ -563,7 +578,8 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
 template <typename Real, int PREC, int MODEL, bool WALL, int KS>
 __global__ void __maxnreg__(FPT_STEPPER_MAXNREG)
 stepper_kernel(const StepperParams P) {
-    static_assert(KS % 4 == 0, "a scheduling block is a whole number of Philox blocks");
+    static_assert(KS % (sizeof(Real) == 4 ? 16 : 4) == 0,
+                  "a scheduling block is a whole number of 16-step groups (binary32) or 4-step blocks (binary64)");
     using Entry = Pending<Real, PREC>;
     // dynamic shared memory: [set table][set starts][per-warp replay queues][parking slots]
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -622,6 +638,15 @@ stepper_kernel(const StepperParams P) {
                         if ((long long)t >= s_first[mid]) lo = mid; else hi = mid - 1;
                     }
                     set = lo;
+                    bool bad_set = false;
+#if FPT_DEBUG
+                    bad_set = lo < 0 || lo >= n_sets || (long long)t < s_first[lo] || (long long)t >= s_first[lo + 1];
+                    if (bad_set) {
+                        atomicOr(&P.scratch->status, kStatusSetIndex);
+                        exhausted = true;  // stop this lane rather than write a record of the wrong set
+                    }
+#endif
+                    if (!bad_set) {
                     const SetConst& S = s_sets[set];
                     rec = t;
                     pl = philox_lane(S.traj_offset + (t - (unsigned long long)S.first), S.set_id, P.keys);
@@ -639,6 +664,7 @@ stepper_kernel(const StepperParams P) {
                     } else {
                         live = true;
                     }
+                    }  // !bad_set
                 }
             }
         }
@@ -649,14 +675,19 @@ stepper_kernel(const StepperParams P) {
         const int m0 = m;
         Real mn = phi;
         Real sblk = (Real)0;
-        const uint32_t k0 = (uint32_t)m0 >> 2;
+        if constexpr (sizeof(Real) == 4) {
+            const uint32_t G0 = (uint32_t)m0 >> 4;
 #pragma unroll
-        for (int g = 0; g < KS / 4; ++g) {
-            if constexpr (sizeof(Real) == 4 && is_pow_model(MODEL)) {
-                steps4_pow<MODEL, WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
-            } else if constexpr (sizeof(Real) == 4) {
-                steps4_f32<WALL>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
-            } else {
+            for (int g = 0; g < KS / 16; ++g) {
+                if constexpr (is_pow_model(MODEL))
+                    steps16_pow<MODEL, WALL>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
+                else
+                    steps16_f32<WALL>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
+            }
+        } else {
+            const uint32_t k0 = (uint32_t)m0 >> 2;
+#pragma unroll
+            for (int g = 0; g < KS / 4; ++g) {
                 Real xi[4];
                 normals4<Real>(pl, k0 + (uint32_t)g, P.keys, xi);
 #pragma unroll
@@ -678,15 +709,26 @@ stepper_kernel(const StepperParams P) {
         if (ev) {
             // finished inside this block: queue the block-start state, free the lane
             if (event) {
-                Entry& slot = q[q_count + __popc(ev & lt_mask)];
-                slot.rec = rec;
-                slot.m0 = m0;
-                slot.set = set;
-                slot.phi0 = phi0;
-                slot.W = W;
+                const int at = q_count + __popc(ev & lt_mask);
+#if FPT_DEBUG
+                if (at >= kQueueCap) {
+                    atomicOr(&P.scratch->status, kStatusQueueFull);  // the run is dropped, not written
+                } else
+#endif
+                {
+                    Entry& slot = q[at];
+                    slot.rec = rec;
+                    slot.m0 = m0;
+                    slot.set = set;
+                    slot.phi0 = phi0;
+                    slot.W = W;
+                }
                 live = false;
             }
             q_count += __popc(ev);
+#if FPT_DEBUG
+            if (q_count > kQueueCap) q_count = kQueueCap;
+#endif
             if (q_count >= 32) {
                 // park this lane's run (the stride keeps one thread's words in one bank)
                 const int stride = (int)blockDim.x;

@@ -21,7 +21,6 @@ StepperKernel make() {
 template <int PREC, int MODEL, bool WALL>
 StepperKernel by_ks(int ks) {
     switch (ks) {
-        case 8: return make<PREC, MODEL, WALL, 8>();
         case 16: return make<PREC, MODEL, WALL, 16>();
         case 32: return make<PREC, MODEL, WALL, 32>();
         case 64: return make<PREC, MODEL, WALL, 64>();

@@ -75,29 +75,31 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
     float ph = e.phi0, prev = e.phi0, s2 = 0.f;
     int M = 0;
     bool crossed = false;
-    const uint32_t k0 = (uint32_t)e.m0 >> 2;
     if (have) {
-        for (int g = 0; g < KS / 4; ++g) {
-            uint32_t w[4];
-            philox_block(pl, k0 + (uint32_t)g, P.keys, w);
+        for (int gg = 0; gg < KS / 16; ++gg) {
+            uint32_t V[12];
+            philox_group(pl, ((uint32_t)e.m0 >> 4) + (uint32_t)gg, P.keys, V);
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const NormalPair np = normal_pair_f32(w[2 * p], w[2 * p + 1]);
-                const float q = __fmul_rn(model.kq, np.rho);
+            for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (M == 0) {
-                        const float trig = h == 0 ? np.c : np.s;
-                        prev = ph;
-                        ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
-                        ph = fminf(ph, twouv - ph);
-                        s2 = __fmaf_rn(np.rho, trig, s2);
-                        const int step_index = e.m0 + 4 * g + 2 * p + h;
-                        if (ph <= phi_end) {
-                            crossed = true;
-                            M = step_index + 1;
-                        } else if (step_index + 1 >= S.m_max) {
-                            M = step_index + 1;
+                for (int p = 0; p < 2; ++p) {
+                    const NormalPair np = group_pair_f32(V, j, p);
+                    const float q = __fmul_rn(model.kq, np.rho);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (M == 0) {
+                            const float trig = h == 0 ? np.c : np.s;
+                            prev = ph;
+                            ph = model.step(ph, __fmaf_rn(q, trig, model.tc));
+                            ph = fminf(ph, twouv - ph);
+                            s2 = __fmaf_rn(np.rho, trig, s2);
+                            const int step_index = e.m0 + 16 * gg + 4 * j + 2 * p + h;
+                            if (ph <= phi_end) {
+                                crossed = true;
+                                M = step_index + 1;
+                            } else if (step_index + 1 >= S.m_max) {
+                                M = step_index + 1;
+                            }
                         }
                     }
                 }
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams
     // nothing between two bias evaluations (mlp_tile_forward waits for the
     // last MMA that reads it)
     static_assert(sizeof(F.A) >= 128 * 10 * 4, "park area");
+    static_assert(KS % 16 == 0, "a bias block is a whole number of 16-step Philox groups");
     volatile unsigned* v = reinterpret_cast<volatile unsigned*>(F.A) + tid;
 
     if (warp == 0) {
@@ -224,10 +227,10 @@ __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams
         const float phi0 = phi;
         const int m0 = m;
         float mn = phi, srho = 0.f;
-        const uint32_t k0 = (uint32_t)m0 >> 2;
+        const uint32_t G0 = (uint32_t)m0 >> 4;
 #pragma unroll
-        for (int g = 0; g < KS / 4; ++g)
-            steps4_f32<true>(model, pl, k0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
+        for (int g = 0; g < KS / 16; ++g)
+            steps16_f32<true>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
         const float sblk = -kSqrt2Ln2 * srho;  // the block's sum of normals
         m = m0 + KS;
         const bool event = live && (mn <= phi_end || m >= m_max);
@@ -349,6 +352,7 @@ using namespace fpt;
 extern "C" int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                                 double* out_N, double* out_logw, fpt_mlp_record* records,
                                 int64_t record_capacity, int64_t* n_records_out) {
+    NvtxRange nvtx_range("fpt_simulate_mlp");
     if (!p) return fail(FPT_EINVAL, "params is NULL");
     if (p->bias_kind != FPT_BIAS_MLP) return fail(FPT_EINVAL, "fpt_simulate_mlp needs bias_kind FPT_BIAS_MLP");
     if (!p->mlp) return fail(FPT_EINVAL, "mlp parameters are NULL");
@@ -378,7 +382,7 @@ extern "C" int fpt_simulate_mlp(const fpt_params* p, const fpt_set* sets, int32_
     workspace_image(P, L, &img);
     const size_t off_cnt = L.bytes;
     unsigned char* ws = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.bytes + 256, st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&ws), L.bytes + 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     std::vector<unsigned char> img2(img);
     img2.resize(L.bytes + 256, 0);

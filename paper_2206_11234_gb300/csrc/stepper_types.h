@@ -4,6 +4,7 @@
 
 #include "fpt.h"
 #include "rng.cuh"
+#include "status.h"
 
 namespace fpt {
 

@@ -131,6 +131,7 @@ using namespace fpt;
 
 extern "C" int fpt_mlp_train_step(const fpt_params* p, const fpt_set* set, uint64_t seed, double tail_N,
                                   double lr, fpt_mlp_train_state* S, fpt_mlp_train_stats* stats) {
+    NvtxRange nvtx_range("fpt_mlp_train_step");
     if (!p || !set || !S) return fail(FPT_EINVAL, "NULL argument");
     if (p->mlp != S->w) return fail(FPT_EINVAL, "p->mlp must be the state's BF16 parameters");
     if (!S->master || !S->adam_m || !S->adam_v || !S->grad || !S->w || !S->records || !S->out_N ||
@@ -144,7 +145,7 @@ extern "C" int fpt_mlp_train_step(const fpt_params* p, const fpt_set* set, uint6
     if (rc) return rc;
     const long long n = set->n_traj;
     TailAcc* acc = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&acc), sizeof(TailAcc), st);
+    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&acc), sizeof(TailAcc), st);
     if (e != cudaSuccess) return cuda_fail(e, "training scratch");
     cudaMemsetAsync(acc, 0, sizeof(TailAcc), st);
     int n_sm = 0;

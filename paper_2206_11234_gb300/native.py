@@ -16,7 +16,7 @@ from . import build as _build
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-FPT_ABI_VERSION = 2
+FPT_ABI_VERSION = 3
 FPT_OK = 0
 FPT_EINVAL = -1
 FPT_ECUDA = -2
@@ -62,6 +62,15 @@ class FptParams(ctypes.Structure):
     ]
 
 
+class FptPipeRates(ctypes.Structure):
+    _fields_ = [
+        ("fp64_fma_per_s", ctypes.c_double),
+        ("xu_lg2_per_s", ctypes.c_double),
+        ("wide_mul_per_s", ctypes.c_double),
+        ("fp32_fma_per_s", ctypes.c_double),
+    ]
+
+
 class FptSet(ctypes.Structure):
     _fields_ = [
         ("phi_in", ctypes.c_double),
@@ -87,7 +96,8 @@ class FptBin(ctypes.Structure):
 
 
 ESTIMATE_FIELDS = ("count", "p_direct", "se_direct", "p_lognormal", "eps_lo", "eps_hi", "mean_lw", "var_lw",
-                   "skew", "kurt", "z_skew", "z_kurt", "k2", "p_normal", "jk_direct", "jk_lognormal")
+                   "skew", "kurt", "z_skew", "z_kurt", "k2", "p_normal", "jk_direct", "jk_lognormal",
+                   "bias_ln", "bias_se")
 
 
 class FptEstimateBin(ctypes.Structure):
@@ -120,12 +130,17 @@ class FptError(RuntimeError):
         self.code = code
 
 
+# FPT_DEBUG_LIB=1: load the build with device bounds checks (build.py --debug)
+DEBUG_LIB = os.environ.get("FPT_DEBUG_LIB", "0") == "1"
+
+
 def _load():
-    path = os.path.join(HERE, "libfpt_gb300.so")
+    path = _build.lib_path(DEBUG_LIB)
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_2206_11234_gb300/build.py "
-                          "(python -c 'import __graft_entry__ as g; g.build()')")
-    if not _build.up_to_date():
+                          "(python -c 'import __graft_entry__ as g; g.build()'" +
+                          (", or build.py --debug for the checked build)" if DEBUG_LIB else ")"))
+    if not _build.up_to_date(DEBUG_LIB):
         raise ImportError(f"{path} is older than its sources: rebuild it")
     L = ctypes.CDLL(path)
     P = ctypes.POINTER
@@ -150,6 +165,14 @@ def _load():
     L.fpt_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.fpt_wait_selftest.argtypes = [P(i32), P(d), vp]
     L.fpt_wait_selftest.restype = ctypes.c_int
+    L.fpt_inject_alloc_failures.argtypes = [i32]
+    L.fpt_inject_alloc_failures.restype = ctypes.c_int
+    L.fpt_inject_status.argtypes = [u32]
+    L.fpt_inject_status.restype = ctypes.c_int
+    L.fpt_hist_merge.argtypes = [vp, i32, i64, vp, vp, vp]
+    L.fpt_hist_merge.restype = ctypes.c_int
+    L.fpt_pipe_rates.argtypes = [P(FptPipeRates), vp]
+    L.fpt_pipe_rates.restype = ctypes.c_int
     L.fpt_autotune_reset.argtypes = []
     L.fpt_autotune_reset.restype = None
     L.fpt_strerror.restype = ctypes.c_char_p
@@ -325,7 +348,7 @@ def fpt_stitch(estimates: torch.Tensor, out: Optional[torch.Tensor] = None, *, e
     fpt_estimate outputs of several simulations over the same bins) ->
     float64[n_bins, 6] (STITCH_FIELDS)."""
     if estimates.dim() != 3 or estimates.shape[2] != len(ESTIMATE_FIELDS) or estimates.dtype != torch.float64:
-        raise ValueError("estimates must be float64[n_runs, n_bins, 16]")
+        raise ValueError(f"estimates must be float64[n_runs, n_bins, {len(ESTIMATE_FIELDS)}]")
     n_runs, n_bins = estimates.shape[0], estimates.shape[1]
     if out is None:
         out = torch.empty((n_bins, len(STITCH_FIELDS)), dtype=torch.float64, device=estimates.device)
@@ -458,6 +481,32 @@ def fpt_autotune(params: FptParams, sets: ctypes.Array, seed: int = 0, fraction:
 
 def fpt_autotune_reset():
     lib.fpt_autotune_reset()
+
+
+def fpt_hist_merge(parts, part_counts=None):
+    """Histogram of the union of disjoint run sets.  parts: float64 array
+    [n_parts, n_bins, BIN_FIELDS] (host; fpt_bin layout, count as int64 bits);
+    part_counts: int64 [n_parts, 4] or None.  Returns (bins [n_bins, BIN_FIELDS],
+    counts [4] or None) as host tensors."""
+    p = torch.as_tensor(parts).detach().to("cpu", torch.float64).contiguous()
+    if p.dim() != 3 or p.shape[2] != BIN_FIELDS:
+        raise ValueError("parts must be [n_parts, n_bins, BIN_FIELDS]")
+    out = torch.empty((p.shape[1], BIN_FIELDS), dtype=torch.float64)
+    pc = oc = None
+    if part_counts is not None:
+        pc = torch.as_tensor(part_counts).detach().to("cpu", torch.int64).contiguous()
+        oc = torch.empty(4, dtype=torch.int64)
+    _check(lib.fpt_hist_merge(p.data_ptr(), p.shape[0], p.shape[1], None if pc is None else pc.data_ptr(),
+                              out.data_ptr(), None if oc is None else oc.data_ptr()))
+    return out, oc
+
+
+def fpt_pipe_rates(stream=None) -> dict:
+    """Measured thread operations per second of the FP64 FMA, XU (lg2), wide
+    integer multiply and FP32 FMA pipes of the current device."""
+    r = FptPipeRates()
+    _check(lib.fpt_pipe_rates(ctypes.byref(r), _stream(stream)))
+    return {name: getattr(r, name) for name, _ in FptPipeRates._fields_}
 
 
 def fpt_wait_selftest(stream=None):

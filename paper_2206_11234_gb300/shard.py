@@ -6,12 +6,12 @@ because each run's noise is a function of (seed, set id, run id) the union of
 the shards is bit-identical to the one-process result.  Nothing is exchanged
 on the data path; the only reduction is the optional merge of the per-rank
 weighted histograms, whose bins carry max-shifted sums (max ln w, sum w/e^max,
-sum w^2/e^(2 max), sum x^k for k = 1..4 with x = ln w - max, count) and merge
-by rescaling to the common maximum (binomial re-centring of the moments).
+sum w^2/e^(2 max), sum x^k for k = 1..4 with x = ln w - max, count): they are
+gathered here and merged by the library (fpt_hist_merge: rescaling to the
+common maximum, binomial re-centring of the moments).
 """
 import copy
-import math
-from typing import List, Sequence, Tuple
+from typing import Sequence
 
 import numpy as np
 
@@ -31,40 +31,32 @@ def shard_sets(specs: Sequence, rank: int, world: int) -> list:
     return out
 
 
-def merge_bins(fields: Sequence[np.ndarray], counts: Sequence[np.ndarray]) -> Tuple[np.ndarray, np.ndarray]:
-    """Merge histograms of disjoint run sets.  fields[r]: float64 [..., 7] with
-    (max_lw, s1, s2, l1, l2, l3, l4); counts[r]: int64 [...].  Empty bins have
-    max_lw = -inf and zero sums."""
-    F = np.stack([np.asarray(f, dtype=np.float64) for f in fields])
-    C = np.stack([np.asarray(c, dtype=np.int64) for c in counts])
-    mx = F[..., 0].max(axis=0)
-    live = np.isfinite(F[..., 0])
-    with np.errstate(invalid="ignore", over="ignore"):
-        scale = np.where(live, np.exp(F[..., 0] - mx), 0.0)
-        delta = np.where(live, F[..., 0] - mx, 0.0)  # <= 0: shift of each part's moments
-    out = np.empty(F.shape[1:], dtype=np.float64)
-    out[..., 0] = mx
-    out[..., 1] = (F[..., 1] * scale).sum(axis=0)
-    out[..., 2] = (F[..., 2] * scale * scale).sum(axis=0)
-    # sum (x + delta)^k = sum_i C(k, i) delta^(k - i) sum x^i, with sum x^0 = count
-    L = [C.astype(np.float64)] + [F[..., 2 + i] for i in range(1, 5)]
-    for k in range(1, 5):
-        acc = np.zeros_like(L[0])
-        for i in range(k + 1):
-            acc += math.comb(k, i) * delta ** (k - i) * L[i]
-        out[..., 2 + k] = np.where(live, acc, 0.0).sum(axis=0)
-    return out, C.sum(axis=0)
+def pack_bins(fields: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    """fpt_bin layout: float64 [n, 8] from fields [n, 7] and int64 counts [n]
+    (the count stored as the bits of an int64)."""
+    out = np.empty((np.asarray(fields).shape[0], 8), dtype=np.float64)
+    out[:, :7] = fields
+    out.view(np.int64)[:, 7] = np.asarray(counts, dtype=np.int64)
+    return out
 
 
-def allgather_merge(fields: np.ndarray, counts: np.ndarray, group=None) -> Tuple[np.ndarray, np.ndarray]:
-    """Merge every rank's histogram with torch.distributed (any backend)."""
+def allgather_merge(bins, counts=None, group=None):
+    """Every rank's histogram gathered with torch.distributed and merged by
+    the library's fpt_hist_merge.  bins: this rank's bins as a float64 tensor
+    [n_bins, 8] in fpt_bin layout, on the device the process group's backend
+    works on (CUDA for NCCL, CPU for gloo); counts: int64 [4] or None.
+    Returns the merged (bins, counts) as host tensors on every rank."""
     import torch
     import torch.distributed as dist
+    from . import native
     world = dist.get_world_size(group)
-    f = torch.from_numpy(np.ascontiguousarray(fields, dtype=np.float64))
-    c = torch.from_numpy(np.ascontiguousarray(counts, dtype=np.int64))
-    fs = [torch.empty_like(f) for _ in range(world)]
-    cs = [torch.empty_like(c) for _ in range(world)]
-    dist.all_gather(fs, f, group=group)
-    dist.all_gather(cs, c, group=group)
-    return merge_bins([x.numpy() for x in fs], [x.numpy() for x in cs])
+    b = torch.as_tensor(bins).contiguous()
+    parts = [torch.empty_like(b) for _ in range(world)]
+    dist.all_gather(parts, b, group=group)
+    cparts = None
+    if counts is not None:
+        c = torch.as_tensor(counts).to(b.device).contiguous()
+        cl = [torch.empty_like(c) for _ in range(world)]
+        dist.all_gather(cl, c, group=group)
+        cparts = torch.stack([x.cpu() for x in cl])
+    return native.fpt_hist_merge(torch.stack([x.cpu() for x in parts]), cparts)

@@ -558,3 +558,73 @@ class FourierDensity:
     def bin_average(self, lo, hi, nodes=8):
         x, w = np.polynomial.legendre.leggauss(nodes)
         return 0.5 * float(np.sum(w * self.pdf(0.5 * (hi - lo) * x + 0.5 * (hi + lo))))
+
+
+# ---------------------------------------------------------------------------
+# No reflecting wall (phi_uv -> infinity): Appendix A's branch-cut integral
+# ---------------------------------------------------------------------------
+def no_wall_chi(t, m, phi, phi_end=math.sqrt(2.0), dps=50):
+    """chi(t, phi) = E[e^{itN}] without a wall, Appendix A (infinite phi_uv):
+    only the g branch of Eq. (A.11) stays bounded as v -> infinity, so
+    chi = g(t, phi) / g(t, phi_end), with alpha(t) = sqrt(1 - 4 i t / v0) on the
+    principal branch.  t may be complex (an mpmath number or a Python complex)."""
+    mp = _mp()
+    mp.mp.dps = dps
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+    al = mp.sqrt(1 - 4j * mp.mpmathify(t) / v0)
+    g, _ = _quad_f(mp, m, -al, phi)
+    ge, _ = _quad_f(mp, m, -al, phi_end)
+    return g / ge
+
+
+def no_wall_im_chi_on_cut(y, m, phi, phi_end=math.sqrt(2.0), dps=50):
+    """Im chi(-i y + 0, phi) for y > v0/4: on the negative imaginary t axis
+    approached from Re t > 0, where 1 - 4 i t / v0 = 1 - 4 y / v0 - i 0 and
+    alpha = -i kappa, kappa = sqrt(4 y / v0 - 1)."""
+    mp = _mp()
+    mp.mp.dps = dps
+    v0 = mp.mpf(m) ** 2 / (48 * mp.pi ** 2)
+    kappa = mp.sqrt(4 * mp.mpf(y) / v0 - 1)
+    al = -1j * kappa
+    g, _ = _quad_f(mp, m, -al, phi)
+    ge, _ = _quad_f(mp, m, -al, phi_end)
+    return float(mp.im(g / ge))
+
+
+def no_wall_branch_cut(m, phi, N_min, phi_end=math.sqrt(2.0), nodes=1600, dps=50, tol=1e-18):
+    """The first-passage law without a wall, Appendix A (Eq. (A.28)): closing
+    the Fourier inversion P(N) = (1/2pi) int e^{-itN} chi(t) dt (Eq. (A.6))
+    around the branch cut of alpha(t) on t = -i y, y > v0/4 (chi has no poles
+    there), with chi(-iy - 0) = conj chi(-iy + 0), gives
+        P(N) = (1/pi) int_{v0/4}^inf Im chi(-iy + 0, phi) e^{-yN} dy,
+        Q(N) = P(N' > N) = (1/pi) int_{v0/4}^inf Im chi(-iy + 0, phi) e^{-yN} / y dy.
+    (The printed prefactor, -2 in place of 1/pi, is read as garbled: with it
+    the density is neither positive nor normalised.)  With y = v0/4 + s^2 the
+    square-root onset at the branch point becomes a smooth integrand, taken by
+    Gauss-Legendre on [0, s_max].  |chi| grows along the cut roughly like
+    exp(c sqrt(y)), so the Laplace form suits N >= N_min with s_max chosen
+    where e^{-y N_min} |Im chi| < tol.  Returns (P, Q) as functions of an
+    array of N >= N_min."""
+    v0 = m * m / (48.0 * math.pi ** 2)
+    y0 = v0 / 4.0
+    s_max = 1.0
+    while True:
+        y = y0 + s_max * s_max
+        if abs(no_wall_im_chi_on_cut(y, m, phi, phi_end, dps)) * math.exp(-y * N_min) < tol:
+            break
+        s_max *= 1.5
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    s = 0.5 * s_max * (x + 1.0)
+    ws = 0.5 * s_max * w * 2.0 * s  # dy = 2 s ds
+    y = y0 + s * s
+    im = np.array([no_wall_im_chi_on_cut(yy, m, phi, phi_end, dps) for yy in y])
+
+    def P(N):
+        N = np.atleast_1d(np.asarray(N, dtype=float))
+        return (np.exp(-np.outer(N, y)) * (ws * im)).sum(axis=1) / math.pi
+
+    def Q(N):
+        N = np.atleast_1d(np.asarray(N, dtype=float))
+        return (np.exp(-np.outer(N, y)) * (ws * im / y)).sum(axis=1) / math.pi
+
+    return P, Q

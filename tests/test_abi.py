@@ -39,7 +39,7 @@ def test_struct_layouts_match_header(native, tmp_path):
     structs = {"fpt_params": native.FptParams, "fpt_set": native.FptSet, "fpt_bin": native.FptBin,
                "fpt_hist_counts": native.FptHistCounts, "fpt_mlp_train_state": native.FptMlpTrainState,
                "fpt_mlp_train_stats": native.FptMlpTrainStats, "fpt_estimate_bin": native.FptEstimateBin,
-               "fpt_stitch_bin": native.FptStitchBin}
+               "fpt_stitch_bin": native.FptStitchBin, "fpt_pipe_rates_out": native.FptPipeRates}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fpt.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -168,3 +168,10 @@ def test_strerror_names_every_code(native):
         assert L.fpt_strerror(code) != b"unknown error"
     assert L.fpt_strerror(-99) == b"unknown error"
     assert L.fpt_abi_version() == native.FPT_ABI_VERSION
+
+
+def test_injection_entries_validate_on_the_host(native):
+    L = native.lib
+    assert L.fpt_inject_alloc_failures(-1) == native.FPT_EINVAL
+    assert L.fpt_inject_alloc_failures(0) == native.FPT_OK
+    assert L.fpt_inject_status(0) == native.FPT_OK

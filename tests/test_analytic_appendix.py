@@ -7,6 +7,14 @@ decay rates of the finite-difference generator; P(N) and Q(N) summed over the
 poles with the residues of Eq. (A.18) equal the survival PDE's, and the
 oracle's weighted tail agrees with them.
 
+Appendix A without a wall (phi_uv -> infinity): the characteristic function
+g(t, phi)/g(t, phi_end) has the mean of Eq. (19) and chi(0) = 1; the density
+from the branch-cut integral (Eq. (A.28), prefactor 1/pi) is positive, its
+survival function equals the survival PDE's with a far wall where the wall no
+longer matters, its own derivative matches the density, the quadrature has
+converged, and the far tail approaches the N^{-3/2} e^{-v0 N/4} law the
+appendix derives, with a 1/N correction.
+
 Appendix B: the Edgeworth expansion of Eq. (B.10) with He_3 = x^3 - 3x has the
 moments it is built from (the printed He_3 = x^2 - 1 would change the
 variance); the cumulants from the backward equations match the oracle's runs,
@@ -155,3 +163,37 @@ def test_edgeworth_fits_the_peak(interim_runs):
     chi_g = np.sum((cnt - exp_g) ** 2 / exp_g) / cnt.size
     assert chi_e < 2.0, chi_e
     assert chi_g > 2 * chi_e and chi_g > 3.0, (chi_g, chi_e)
+
+
+def test_no_wall_branch_cut_integral():
+    import mpmath as mp
+    m, phi = 1.0, math.sqrt(42.0)
+    v0 = m * m / (48 * math.pi ** 2)
+    y0 = v0 / 4
+    # the closed-form characteristic function: chi(0) = 1 and the mean of Eq. (19)
+    h = 1e-6
+    lnM = lambda s: float(mp.log(mp.re(A.no_wall_chi(-1j * s, m, phi))))
+    assert abs(lnM(0.0)) < 1e-30
+    mean = (lnM(h) - lnM(-h)) / (2 * h)
+    assert abs(mean / A.mean_fpt_quad(phi, m) - 1) < 1e-8, mean
+    P, Q = A.no_wall_branch_cut(m, phi, 6.0, nodes=600)
+    N = np.array([6.0, 8.0, 10.0, 15.0, 20.0, 30.0])
+    # survival PDE with the wall at 20 (a wall at 30 changes these by < 1e-5)
+    D, S = _fns(m)
+    Qp = A.survival_pde(phi, D, S, SQ2, 20.0, np.concatenate([[0.0], N]), n=6001, dN=2e-3)[1:]
+    np.testing.assert_allclose(Q(N), Qp, rtol=3e-3)
+    # the pair is consistent: P = -dQ/dN
+    dq = (Q(N - 1e-4) - Q(N + 1e-4)) / 2e-4
+    np.testing.assert_allclose(dq, P(N), rtol=1e-6)
+    # converged in the number of nodes
+    P2, _ = A.no_wall_branch_cut(m, phi, 6.0, nodes=900)
+    far = np.array([6.0, 10.0, 30.0, 73.0, 300.0, 3000.0])
+    np.testing.assert_allclose(P(far), P2(far), rtol=1e-9)
+    # positive, and the far tail N^{-3/2} e^{-v0 N / 4} A1 / sqrt(pi v0), A1 = lim Im chi / kappa
+    grid = np.geomspace(6.0, 3e4, 60)
+    assert np.all(P(grid) > 0)
+    s = 1e-4
+    A1 = A.no_wall_im_chi_on_cut(y0 + s * s, m, phi) / math.sqrt(4 * s * s / v0)
+    r = lambda n: P(n)[0] * n ** 1.5 * math.exp(y0 * n) / (A1 / math.sqrt(math.pi * v0))
+    r1, r3 = r(1e4) - 1, r(3e4) - 1
+    assert 0 < r3 < 0.05 and 2.5 < r1 / r3 < 3.5, (r1, r3)

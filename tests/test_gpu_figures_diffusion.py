@@ -18,10 +18,9 @@ state with binary64 log-weight sums, dN = 5e-4 (the paper gives no dN).
   each wall's histogram follows its own pole expansion; near the peak the walls
   at 1.2 and 1.4 phi_in give the same density, and they separate only in the
   tail (from N ~ 20 on), which decays at each wall's leading root (0.6528,
-  0.3798, 0.2458).  Without a wall (the paper's phi_uv -> infinity limit, whose
-  branch-cut integral of Eq. (A.28) is not used here) the histogram follows
-  the survival PDE with a far wall, and near the peak equals the 1.4 phi_in
-  wall's.
+  0.3798, 0.2458).  Without a wall (the paper's phi_uv -> infinity limit) the
+  histogram follows the branch-cut integral of Eq. (A.28) bin by bin, with the
+  same bar, and near the peak equals the 1.4 phi_in wall's.
 """
 import math
 
@@ -87,6 +86,11 @@ def _compare(e, P, label, rel_sys=0.03):
     print(f"{label}: {use.sum()} bins, deepest P {deepest:.3e} at N {EDGES[:-1][use][-1]:.1f}, "
           f"max |ln(p/P)| {dev.max():.4f}, max |ln(p/P)|/se {np.max(dev / rel):.2f}, "
           f"jackknife/se median {np.nanmedian(e['jk_direct'][use] / e['se_direct'][use]):.3f}")
+    # the weighted estimator's effective number of runs, (sum w)^2 / sum w^2 ~ (p / se)^2
+    neff = (e["p_direct"][use] / e["se_direct"][use]) ** 2
+    for i in np.argsort(-dev / (4 * rel + rel_sys))[:4]:
+        print(f"   {label} N {EDGES[:-1][use][i]:.1f}: count {int(e['count'][use][i])}, n_eff {neff[i]:.0f}, "
+              f"ln(p/P) {np.log(e['p_direct'][use][i] / P[use][i]):+.3f}, se/p {rel[i]:.3f}")
     assert worst <= 1.0, (label, worst)
     return use, deepest
 
@@ -125,13 +129,11 @@ def test_fig3_wall_at_the_start(nat):
 
 
 def _no_wall_bins():
-    """The phi_uv -> infinity limit: bin averages of the survival PDE with the
-    wall at 20, where it no longer matters (a wall at 30 changes them by < 1e-5
-    out to N = 30)."""
-    D = lambda x: A.quad_drift(x, 0.0, 1.0)
-    S = lambda x: A.quad_noise(x, 1.0)
-    Q = A.survival_pde(R42, D, S, SQ2, 20.0, EDGES, n=6001, dN=2e-3)
-    P = (Q[:-1] - Q[1:]) / WIDTH
+    """The phi_uv -> infinity limit: bin averages (Q(t_j) - Q(t_{j+1})) / d of
+    Appendix A's branch-cut integral (Eq. (A.28))."""
+    _, Q = A.no_wall_branch_cut(1.0, R42, N_FROM, nodes=600)
+    q = Q(EDGES)
+    P = (q[:-1] - q[1:]) / WIDTH
     P[EDGES[:-1] < N_FROM] = np.nan
     return P
 
@@ -145,8 +147,8 @@ def test_fig4_wall_position(nat):
         rate, span = _fit_rate([e], P, 25.0 if u > R42 else 15.0)
         print(f"wall {u / R42:.1f} phi_in: tail rate {rate:.4f}, leading root {lam0:.4f}")
         assert abs(rate / lam0 - 1) < 0.03, (u, rate, lam0)
-    # no wall (the paper's phi_uv -> infinity curve): the far-wall survival PDE,
-    # and near the peak the same density as the wall at 1.4 phi_in
+    # no wall (the paper's phi_uv -> infinity curve): Appendix A's branch-cut
+    # integral, and near the peak the same density as the wall at 1.4 phi_in
     P_inf = _no_wall_bins()
     _compare(es[3], P_inf, "no wall")
     pk = (EDGES[:-1] >= 6.0) & (EDGES[1:] <= 8.0)

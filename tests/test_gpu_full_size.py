@@ -25,8 +25,9 @@ stepper over all sets plus the per-set histograms, seed 0.
   unbiased drift-dominated set against Eq. (19) to 1e-3; E[w] = 1.
 * The drift-dominated ladder in binary32 against the binary64 GPU path on the
   same runs, every bin (the reduced-precision bar: within 3 combined sigma).
-* The learned-bias inference (2^26 runs) against the survival PDE and, on
-  sampled runs, the oracle running the same network.
+* The learned-bias inference (2^26 runs) against the survival PDE, on
+  sampled runs against the oracle running the same network, and bin by bin
+  against 2^15 oracle runs of that network.
 """
 import math
 from concurrent.futures import ThreadPoolExecutor
@@ -37,6 +38,7 @@ import pytest
 import analytic as A
 import oracle
 from paper_2206_11234_gb300 import workloads as W
+from test_gpu_mlp_parity import assert_bins_agree, per_bin_z
 from test_gpu_parity import assert_f64_parity
 
 pytestmark = pytest.mark.gpu
@@ -211,8 +213,11 @@ def test_drift_ladder_binary32_against_binary64_every_bin(nat):
     against the binary64 GPU path on the same runs.  <N> agrees to 1e-3 (in
     fact ~1e-7); every bin with >= 400 runs agrees within 3 combined standard
     errors, the two estimates treated as independent (they share their noise,
-    so this is conservative: measured at most 0.18); per run, N differs by
-    ~2e-5 (1e-3 sigma_N) and never by a whole step."""
+    so this is loose: measured at most 0.18), and within 3 paired standard
+    errors (the spread of the per-run differences, the resolution at which a
+    systematic shift from binary32 arithmetic would show), the count beyond 3
+    at most the 99.9 % binomial quantile and none beyond 5; per run, N differs
+    by ~2e-5 (1e-3 sigma_N) and never by a whole step."""
     import torch
     wl32 = W.drift_dominated_ladder()
     wl64 = W.drift_dominated_ladder(precision="f64")
@@ -234,7 +239,8 @@ def test_drift_ladder_binary32_against_binary64_every_bin(nat):
     # differs by that step's increment b sqrt(dN) |xi| < 6 b sqrt(dN)
     assert np.quantile(dn, 0.9999) < 0.01 * 0.0203 and dn.max() < 1e-3
     assert np.median(lw_d) < 1e-4 and lw_d.max() < 6 * 4.0 * math.sqrt(1e-3)
-    worst = []
+    from scipy.stats import binom
+    worst, paired = [], []
     for s in range(len(wl32.sets)):
         sl = slice(s * n, (s + 1) * n)
         assert abs(N32[sl].mean() / N64[sl].mean() - 1) < 1e-3
@@ -254,7 +260,30 @@ def test_drift_ladder_binary32_against_binary64_every_bin(nat):
         worst.append(float(z.max()))
         assert use.sum() >= 10
         assert np.all(z <= 3.0), (s, z.max())
+        # paired: both precisions ran the same runs, so the standard error of the
+        # difference is that of the per-run differences of the bin's weighted
+        # indicator, sqrt(var_i(w32_i 1{i in j under binary32} - w64_i 1{i in j
+        # under binary64}) / n) / d -- orders of magnitude below the combined
+        # one, and the bar at which a systematic binary32 shift would show
+        j32 = np.clip(np.ceil((N32[sl] - 7.0) / 0.0075).astype(np.int64) - 1, -1, 400)
+        j64 = np.clip(np.ceil((N64[sl] - 7.0) / 0.0075).astype(np.int64) - 1, -1, 400)
+        w32 = np.exp(lw32.cpu().numpy()[sl])
+        w64 = np.exp(lw64.cpu().numpy()[sl])
+        inr32, inr64 = (j32 >= 0) & (j32 < 400), (j64 >= 0) & (j64 < 400)
+        same = (j32 == j64) & inr32
+        d1 = np.bincount(j32[inr32], w32[inr32], 400) - np.bincount(j64[inr64], w64[inr64], 400)
+        d2 = (np.bincount(j32[same], (w32[same] - w64[same]) ** 2, 400)
+              + np.bincount(j32[inr32 & ~same], w32[inr32 & ~same] ** 2, 400)
+              + np.bincount(j64[inr64 & ~same], w64[inr64 & ~same] ** 2, 400))
+        sep = np.sqrt(np.maximum(d2 / n - (d1 / n) ** 2, 0.0) / n)
+        ok = use & (sep > 0)
+        zp = (d1[ok] / n) / sep[ok]
+        allowed = int(binom.ppf(0.999, ok.sum(), 0.0027))
+        paired.append((float(np.abs(zp).max()), int(np.sum(np.abs(zp) > 3)), allowed,
+                       float(np.median(sep[ok] / np.hypot(e1[ok], e2[ok]) * 0.0075))))
+        assert np.sum(np.abs(zp) > 3) <= allowed and np.abs(zp).max() < 5, (s, paired[-1])
     print("max |P32 - P64| / combined sigma per set:", [round(w, 3) for w in worst])
+    print("paired: (max |z|, bins beyond 3, allowed, paired / combined sigma) per set:", paired)
 
 
 def test_learned_bias_inference_full_size(nat):
@@ -265,7 +294,8 @@ def test_learned_bias_inference_full_size(nat):
     within 4 standard errors + 0.5 %; runs sampled over the id range follow
     the oracle running the same BF16 network in binary64 (the paths differ
     only through the BF16 evaluation of b, so the medians of the per-run
-    differences are small; a few runs drift apart)."""
+    differences are small; a few runs drift apart); and the weighted P(N)
+    agrees with 2^15 oracle runs of the same network bin by bin."""
     import torch
     norm = (5.2, 0.5, 30.0, 1.0 / 15.0)
     params = W.mlp_params(seed=5, gain=1.0, out_scale=0.05)
@@ -306,3 +336,15 @@ def test_learned_bias_inference_full_size(nat):
           f"{np.quantile(dl, 0.9):.2e}")
     assert np.mean(np.isinf(gN) == np.isinf(oN)) >= 0.95
     assert np.median(dn) < 5e-3 and np.median(dl) < 0.05
+    # the weighted P(N) bin by bin (width 1 on (0, 60]) against 2^15 oracle runs of the same network
+    m_o, chunk = 1 << 15, 1 << 11
+
+    def part(k):
+        r = oracle.make_run(m=1.0, phi_in=8.0, phi_uv=9.0, dN=5e-4, n_max=60.0, seed=seed + 1, traj_offset=k * chunk,
+                            mlp=p64, mlp_norm=norm, k_eval=64)
+        return oracle.simulate(r, chunk)[:2]
+    with ThreadPoolExecutor(16) as ex:
+        res = list(ex.map(part, range(m_o // chunk)))
+    z = per_bin_z(N.cpu().numpy(), lw.cpu().numpy(), np.concatenate([a for a, _ in res]),
+                  np.concatenate([b for _, b in res]), np.arange(0.0, 61.0, 1.0))
+    assert_bins_agree(z, "learned bias at 2^26 runs vs 2^15 oracle runs")

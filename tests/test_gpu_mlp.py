@@ -43,7 +43,7 @@ def test_mlp_forward_matches_oracle(nat, n):
     out = torch.empty(n, dtype=torch.float32, device="cuda")
     nat.fpt_mlp_forward(w, torch.from_numpy(phi).cuda(), torch.from_numpy(N).cuda(), out)
     got = out.cpu().numpy().astype(np.float64)
-    m = min(n, 3000)
+    m = n
     ref = np.array([oracle.mlp_forward(p64, NORM, float(phi[i]), float(N[i]))[0] for i in range(m)])
     scale = np.abs(p64[-65:-1]).sum()
     err = np.abs(got[:m] - ref)

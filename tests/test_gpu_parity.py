@@ -121,7 +121,7 @@ def test_f64_per_run_parity(nat, case):
 
 
 @pytest.mark.parametrize("precision,block_dim,k_steps", [("f64", 32, 4), ("f64", 512, 4),
-                                                         ("f64", 64, 8), ("f32_kahan", 64, 8),
+                                                         ("f64", 64, 8), ("f32_kahan", 64, 64),
                                                          ("f32_f64acc", 512, 32)])
 def test_results_independent_of_launch_shape(nat, precision, block_dim, k_steps):
     """Records do not depend on the block size; the block length k_steps only

@@ -199,3 +199,61 @@ def test_stitch_error_covers_the_truth():
         o = E.stitch(ests, p_threshold=0.0)
         hit += (o["p"][0] - o["eps_lo"][0] <= truth <= o["p"][0] + o["eps_hi"][0])
     assert 0.58 <= hit / reps <= 0.80, hit / reps
+
+
+def test_bias_terms_match_kstat_and_their_spread():
+    """bias_ln = k3/6 + k4/24 with scipy's unbiased k-statistics; bias_se is
+    the spread of that quantity over normal samples (Fisher's variances)."""
+    rng = np.random.default_rng(8)
+    for n in (4, 9, 50, 3000):
+        x = rng.gamma(3.0, 1.0, n) - 7.0
+        b, se = E.lognormal_bias(x)
+        assert math.isclose(b, stats.kstat(x, 3) / 6 + stats.kstat(x, 4) / 24, rel_tol=1e-9, abs_tol=1e-12)
+        assert se > 0
+    for n in (50, 200, 2000):
+        sig = 2.5
+        draws = [E.lognormal_bias(rng.normal(1.0, sig, n)) for _ in range(4000)]
+        b = np.array([d[0] for d in draws])
+        se = np.array([d[1] for d in draws])
+        # the spread of the estimate is the standard error at the true variance;
+        # the estimated standard error (through k2) approaches it as n grows
+        v = sig ** 2
+        true_se = math.sqrt(6 * n * v ** 3 / ((n - 1) * (n - 2)) / 36 + 24 * n * (n + 1) * v ** 4 / ((n - 1) * (n - 2) * (n - 3)) / 576)
+        assert abs(b.std() / true_se - 1) < 0.06, (n, b.std(), true_se)
+        assert abs(b.mean()) < 4 * b.std() / math.sqrt(b.size)
+        if n >= 2000:
+            assert abs(np.median(se) / true_se - 1) < 0.05
+    assert all(math.isnan(v) for v in E.lognormal_bias([1.0, 2.0, 3.0]))
+    assert all(math.isnan(v) for v in E.lognormal_bias([1.0] * 10))
+
+
+@pytest.mark.parametrize("sigma2,skew,n", [(31.0, -3e-3, 100000), (31.0, 0.05, 100000), (4.0, 0.2, 20000)])
+def test_bias_terms_correct_the_lognormal_estimate(sigma2, skew, n):
+    """ln w = c + sign sigma (G - k)/sqrt(k), G ~ Gamma(k, 1): variance sigma^2,
+    skewness sign 2/sqrt(k), and ln <w> = c - sign sigma sqrt(k) - k ln(1 - sign
+    sigma / sqrt(k)) exactly.  Eq. (22)'s estimate misses ln <w> by about
+    k3/6 + k4/24; adding bias_ln removes that within its error bias_se, over
+    repeated bins, and the corrected interval covers the truth."""
+    rng = np.random.default_rng(int(1e4 * abs(skew)) + int(sigma2))
+    sig, sgn = math.sqrt(sigma2), math.copysign(1.0, skew)
+    k = (2.0 / abs(skew)) ** 2
+    c = -40.0
+    x = sgn * sig / math.sqrt(k)
+    truth = c - sgn * sig * math.sqrt(k) - k * math.log1p(-x)
+    miss, dev, cover = [], [], 0
+    reps = 40
+    for r in range(reps):
+        lw = c + sgn * sig * (rng.gamma(k, 1.0, n) - k) / math.sqrt(k)
+        o = E.estimate(np.full(n, 0.5), lw, 1, 0.0, 1.0)
+        ln_p = math.log(o["p_lognormal"][0])  # d = 1 and n_total = n_j: the estimate of <w>
+        miss.append(ln_p - truth)
+        d = ln_p + o["bias_ln"][0] - truth
+        dev.append(d)
+        a = math.sqrt(o["var_lw"][0] / n + o["var_lw"][0] ** 2 / (2 * n - 2))
+        cover += abs(d) <= 2 * math.hypot(o["bias_se"][0], a)
+    expected_miss = -(sgn * 2 * sig ** 3 / math.sqrt(k) / 6 + 6 * sig ** 4 / k / 24)  # -(k3/6 + k4/24)
+    miss, dev = np.array(miss), np.array(dev)
+    se = dev.std(ddof=1) / math.sqrt(reps)
+    assert abs(miss.mean() - expected_miss) < 4 * miss.std(ddof=1) / math.sqrt(reps) + 0.05 * abs(expected_miss)
+    assert abs(dev.mean()) < 4 * se, (dev.mean(), se, miss.mean())
+    assert cover >= 0.85 * reps

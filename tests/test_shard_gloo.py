@@ -1,7 +1,7 @@
 """Multi-rank path on the CPU: two gloo ranks each simulate their shard of the
-run ids (with the FP64 oracle standing in for a GPU) and merge histograms;
-the result equals the one-process run exactly (records, counts, maxima) and
-to 1e-12 (sums)."""
+run ids (with the FP64 oracle standing in for a GPU) and merge histograms
+through the library's fpt_hist_merge (host code, no GPU); the result equals
+the one-process run exactly (records, counts, maxima) and to 1e-12 (sums)."""
 import math
 import os
 import socket
@@ -39,9 +39,11 @@ def _worker(rank, world, port, out_dir):
     spec = W.SetSpec(**SPEC)
     mine = shard.shard_sets([spec], rank, world)[0]
     N, lw, bins, counts = _run(mine)
-    f, c = shard.allgather_merge(bins[:, :7], bins[:, 7].astype(np.int64))
+    mb, mc = shard.allgather_merge(shard.pack_bins(bins[:, :7], bins[:, 7]), counts)
+    f = mb.numpy()[:, :7]
+    c = mb.numpy().view(np.int64)[:, 7]
     np.savez(os.path.join(out_dir, f"r{rank}.npz"), N=N, lw=lw, off=mine.traj_offset, f=f, c=c,
-             cnt=counts)
+             cnt=counts, mc=mc.numpy())
     dist.barrier()
     dist.destroy_process_group()
 
@@ -65,6 +67,8 @@ def test_two_gloo_ranks_match_one_process(tmp_path):
         for k in range(3, 7):
             np.testing.assert_allclose(f[:, k], bins[:, k], rtol=1e-9, atol=1e-9 * np.abs(bins[:, k]).max())
     assert sum(int(p["cnt"][3]) for p in parts) == counts[3]
+    for p in parts:
+        assert np.array_equal(p["mc"], counts)
 
 
 def test_shard_ranges_partition_the_ids():
@@ -80,13 +84,23 @@ def test_shard_ranges_partition_the_ids():
         shard.shard_sets([spec], 2, 2)
 
 
+def _merge(fields, counts):
+    from paper_2206_11234_gb300 import native
+    parts = np.stack([shard.pack_bins(f, c) for f, c in zip(fields, counts)])
+    out, _ = native.fpt_hist_merge(parts)
+    return out.numpy()[:, :7], out.numpy().view(np.int64)[:, 7]
+
+
 def test_merge_handles_empty_bins():
     f1 = np.array([[-np.inf, 0, 0, 0, 0, 0, 0], [1.0, 2.0, 3.0, -1.0, 1.0, -1.0, 1.0]])
     f2 = np.array([[0.5, 1.0, 1.0, 0.0, 0.0, 0.0, 0.0], [-np.inf, 0, 0, 0, 0, 0, 0]])
-    f, c = shard.merge_bins([f1, f2], [np.array([0, 2]), np.array([1, 0])])
+    f, c = _merge([f1, f2], [np.array([0, 2]), np.array([1, 0])])
     assert np.array_equal(c, [1, 2])
     assert f[0, 0] == 0.5 and f[0, 1] == 1.0 and f[1, 1] == 2.0
     assert np.array_equal(f[0, 3:], [0, 0, 0, 0]) and np.array_equal(f[1, 3:], [-1, 1, -1, 1])
+    # a bin empty in every part stays empty
+    fe, ce = _merge([f1[:1], f1[:1]], [np.array([0]), np.array([0])])
+    assert fe[0, 0] == -np.inf and np.all(fe[0, 1:] == 0) and ce[0] == 0
 
 
 def test_merge_recentres_moments():
@@ -100,6 +114,16 @@ def test_merge_recentres_moments():
         y = x - m
         return np.array([m, np.exp(y).sum(), np.exp(2 * y).sum(), y.sum(), (y ** 2).sum(), (y ** 3).sum(),
                          (y ** 4).sum()])
-    f, c = shard.merge_bins([part(a)[None], part(b)[None]], [np.array([50]), np.array([70])])
+    f, c = _merge([part(a)[None], part(b)[None]], [np.array([50]), np.array([70])])
     np.testing.assert_allclose(f[0], part(np.concatenate([a, b])), rtol=1e-12)
     assert c[0] == 120
+
+
+def test_merge_rejects_bad_bins():
+    from paper_2206_11234_gb300 import native
+    bad = np.stack([shard.pack_bins(np.array([[np.nan, 0, 0, 0, 0, 0, 0]]), np.array([1]))])
+    with pytest.raises(native.FptError):
+        native.fpt_hist_merge(bad)
+    neg = np.stack([shard.pack_bins(np.array([[0.0, 1, 1, 0, 0, 0, 0]]), np.array([-1]))])
+    with pytest.raises(native.FptError):
+        native.fpt_hist_merge(neg)

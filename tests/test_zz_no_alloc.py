@@ -82,3 +82,30 @@ def test_noalloc_rejects_more_sets_than_its_scratch_holds(nat):
                                             ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()))
     assert rc == nat.FPT_EINVAL
     assert b"at most" in nat.lib.fpt_last_error()
+
+
+def test_noalloc_power_bias_and_no_step_counter(nat):
+    """The power-law bias (its own stepper instantiation and set-table fields)
+    and a call without the optional step counter (steps_out = NULL) also
+    reproduce the regular entry bit for bit."""
+    specs = [W.SetSpec(phi_in=6.0, m=1e-3, b=0.0, dN=1e-4, n_max=40.0, n_traj=3000, set_id=0),
+             W.SetSpec(phi_in=5.5, m=1e-3, b=0.0, dN=1e-4, n_max=40.0, n_traj=1500, set_id=1)]
+    specs[0].b = 2.0e-6
+    specs[1].b = 1.0e-6
+    sets = nat.make_sets(specs)
+    n = sum(s.n_traj for s in specs)
+    for prec, bias_p in (("f32_f64acc", 3.0), ("f64", 2.5)):
+        p = nat.make_params(precision=prec, m=1e-3, n_max=40.0, bias_p=bias_p)
+        Nr, lwr = _regular(nat, p, sets, 21, n)
+        Nn, lwn = _noalloc(nat, p, sets, 21, n)
+        assert np.isfinite(Nr).mean() > 0.5
+        np.testing.assert_array_equal(Nn, Nr)
+        np.testing.assert_array_equal(lwn, lwr)
+    p = nat.make_params(precision="f32_kahan", m=0.01, n_max=10.0)  # steps_out NULL
+    wl = W.drift_dominated_ladder(scale=1 / 4096)
+    sets = nat.make_sets(wl.sets)
+    n = wl.n_total
+    Nr, lwr = _regular(nat, p, sets, 22, n)
+    Nn, lwn = _noalloc(nat, p, sets, 22, n)
+    np.testing.assert_array_equal(Nn, Nr)
+    np.testing.assert_array_equal(lwn, lwr)
