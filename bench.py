@@ -36,7 +36,7 @@ METRIC = ("trajectory steps/s and far-tail effective samples/s at 1 GB300 vs FP6
 # 6 with the sine and cosine, the noise factor, the noise sum 2, ...); and 5.5
 # for the update in psi = phi / sqrt(2 dN) (reciprocal, one FMA, one add), the
 # noise term t, half a three-way block minimum and the noise sum.
-ALG_INST_PER_STEP = 3 * 38 / 16 + 13 / 2 + 5.5
+ALG_INST_PER_STEP = 3 * 38 / 16 + 16 / 2 + 5.5
 MUFU_PER_STEP = 3.0  # lg2 + sqrt + sin + cos per 2 steps, rcp per step
 WIDE_MUL_PER_STEP = 3 * 19 / 16  # 32x32->64 multiplies: 19 per Philox counter (round 1 folds one)
 ISSUE_PER_SM_CLK = 4.0  # warp-instructions issued per SM per clock (4 schedulers)
@@ -774,8 +774,9 @@ def main():
             nat.fpt_simulate_batch(p64, s64, 1, N64, l64, None, None)
             b_.record(stream)
             torch.cuda.synchronize()
-            extra["f64_gpu_plain"] = {"value": int(steps_ctr.item()) / (a.elapsed_time(b_) / 1e3),
-                                      "unit": "steps/s", "runs": n64, "block_dim": 256, "k_steps": 4}
+            st64 = int(steps_ctr.item())
+            extra["f64_gpu_plain"] = {"value": st64 / (a.elapsed_time(b_) / 1e3), "unit": "steps/s", "runs": n64,
+                                      "steps": st64, "block_dim": 256, "k_steps": 4}
             del N64, l64
 
     # end to end through the host-buffer entry (pinned host memory)
@@ -880,13 +881,18 @@ def main():
         c64 = stepper_counters("f64", f64.get("block_dim"), f64.get("k_steps"), name="stepper_f64_counters.json")
         fp64_peak = rates["fp64_fma_per_s"] / 32  # warp DFMA/s
         if c64:
-            per = c64["inst_fp64"] / (c64["steps"] / 32.0)
+            ws64 = c64["steps"] / 32.0
+            per = c64["inst_fp64"] / ws64
             ach = f64["value"] / 32 * per
+            # the FP64 pipe's busy fraction at the live rate: its ncu cycles per
+            # warp-step (per SM) x warp-steps per second and SM / clock
+            busy = f64["value"] / 32 / n_sm * (c64["fp64_pipe_cycles"] / ws64) / f_max
             f64["roofline"] = {"bound": "fp64", "achieved": ach / 1e9, "peak": fp64_peak / 1e9,
                                "unit": "Gwarp-FP64-inst/s", "frac": ach / fp64_peak,
                                "fp64_inst_per_warp_step": per, "steps_per_s_bound": fp64_peak / per * 32,
-                               "pipe_busy_pct_ncu": c64.get("fp64_pipe_busy_pct"),
-                               "peak_source": "DFMA loop on every SM in this run (fpt_pipe_rates)",
+                               "fp64_pipe_busy_live": busy, "pipe_busy_pct_ncu": c64.get("fp64_pipe_busy_pct"),
+                               "peak_source": "DFMA loop on every SM in this run (fpt_pipe_rates); the stepper's "
+                                              "FP64 instructions also include cheaper ones, so frac can pass 1",
                                "source": "profiles/stepper_f64_counters.json"}
         else:
             f64["roofline"] = {"bound": "fp64", "peak": fp64_peak / 1e9, "unit": "Gwarp-DFMA/s", "frac": None,

@@ -20,7 +20,14 @@ state with binary64 log-weight sums, dN = 5e-4 (the paper gives no dN).
   tail (from N ~ 20 on), which decays at each wall's leading root (0.6528,
   0.3798, 0.2458).  Without a wall (the paper's phi_uv -> infinity limit) the
   histogram follows the branch-cut integral of Eq. (A.28) bin by bin, with the
-  same bar, and near the peak equals the 1.4 phi_in wall's.
+  same bar, and near the peak equals the 1.4 phi_in wall's; so does direct
+  sampling (A = 0, 2^28 runs, w = 1) in every bin with >= 400 runs (to
+  P ~ 3e-6 near N = 55), covering the deep bins where the biased runs'
+  weights spread too widely for the direct estimator (var ln w ~ 5 in a bin,
+  a few hundred effective runs).
+* The comparison is asserted in bins whose weighted estimate rests on >= 400
+  effective runs ((sum w)^2 / sum w^2); the reach is that of bins with >= 400
+  runs, the paper's criterion.
 """
 import math
 
@@ -76,21 +83,32 @@ def _simulate(nat, amps, walls, n, seed):
 
 
 def _compare(e, P, label, rel_sys=0.03):
-    """Bins with >= 400 runs and a converged expansion: |ln(p/P)| <= 4 se/p + rel_sys."""
+    """Bins with >= 400 runs and a converged expansion: |ln(p/P)| <= 4 se/p + rel_sys,
+    asserted where the weighted estimate rests on >= 400 effective runs,
+    n_eff = (sum w)^2 / sum w^2 ~ (p / se)^2 (the 400-run threshold of §2.1
+    applied to the effective count: with fewer, a few large weights carry the
+    estimate and its sample error understates the true one, the sampling
+    problem of §2.4).  Returns the bins used and the deepest P reached by bins
+    with >= 400 runs (the paper's reach)."""
     use = (e["count"] >= 400) & np.isfinite(P) & (e["p_direct"] > 0)
     assert use.sum() >= 5, label
-    dev = np.abs(np.log(e["p_direct"][use] / P[use]))
-    rel = e["se_direct"][use] / e["p_direct"][use]
-    worst = np.max(dev / (4 * rel + rel_sys))
     deepest = P[use][-1]
-    print(f"{label}: {use.sum()} bins, deepest P {deepest:.3e} at N {EDGES[:-1][use][-1]:.1f}, "
+    neff = np.zeros_like(e["p_direct"])
+    ok = use & (e["se_direct"] > 0)
+    neff[ok] = (e["p_direct"][ok] / e["se_direct"][ok]) ** 2
+    neff[use & (e["se_direct"] == 0)] = np.inf
+    chk = use & (neff >= 400)
+    assert chk.sum() >= 5, label
+    dev = np.abs(np.log(e["p_direct"][chk] / P[chk]))
+    rel = e["se_direct"][chk] / e["p_direct"][chk]
+    worst = np.max(dev / (4 * rel + rel_sys))
+    print(f"{label}: {use.sum()} bins (>= 400 runs, deepest P {deepest:.3e} at N {EDGES[:-1][use][-1]:.1f}), "
+          f"{chk.sum()} compared (>= 400 effective, to N {EDGES[:-1][chk][-1]:.1f}, P {P[chk][-1]:.3e}): "
           f"max |ln(p/P)| {dev.max():.4f}, max |ln(p/P)|/se {np.max(dev / rel):.2f}, "
-          f"jackknife/se median {np.nanmedian(e['jk_direct'][use] / e['se_direct'][use]):.3f}")
-    # the weighted estimator's effective number of runs, (sum w)^2 / sum w^2 ~ (p / se)^2
-    neff = (e["p_direct"][use] / e["se_direct"][use]) ** 2
-    for i in np.argsort(-dev / (4 * rel + rel_sys))[:4]:
-        print(f"   {label} N {EDGES[:-1][use][i]:.1f}: count {int(e['count'][use][i])}, n_eff {neff[i]:.0f}, "
-              f"ln(p/P) {np.log(e['p_direct'][use][i] / P[use][i]):+.3f}, se/p {rel[i]:.3f}")
+          f"jackknife/se median {np.nanmedian(e['jk_direct'][chk] / e['se_direct'][chk]):.3f}")
+    for i in np.argsort(-dev / (4 * rel + rel_sys))[:3]:
+        print(f"   {label} N {EDGES[:-1][chk][i]:.1f}: count {int(e['count'][chk][i])}, n_eff {neff[chk][i]:.0f}, "
+              f"ln(p/P) {np.log(e['p_direct'][chk][i] / P[chk][i]):+.3f}, se/p {rel[i]:.3f}")
     assert worst <= 1.0, (label, worst)
     return use, deepest
 
@@ -151,6 +169,10 @@ def test_fig4_wall_position(nat):
     # integral, and near the peak the same density as the wall at 1.4 phi_in
     P_inf = _no_wall_bins()
     _compare(es[3], P_inf, "no wall")
+    # the deep no-wall tail without weights: direct sampling (A = 0, w = 1), 2^28 runs
+    (ed,) = _simulate(nat, (0.0,), (math.inf,), 1 << 28, 7)
+    _, deep_d = _compare(ed, P_inf, "no wall, direct sampling")
+    assert deep_d < 1e-5, deep_d
     pk = (EDGES[:-1] >= 6.0) & (EDGES[1:] <= 8.0)
     d = np.abs(np.log(es[3]["p_direct"][pk] / es[2]["p_direct"][pk]))
     sg = np.hypot(es[3]["se_direct"][pk] / es[3]["p_direct"][pk], es[2]["se_direct"][pk] / es[2]["p_direct"][pk])

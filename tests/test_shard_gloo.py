@@ -127,3 +127,25 @@ def test_merge_rejects_bad_bins():
     neg = np.stack([shard.pack_bins(np.array([[0.0, 1, 1, 0, 0, 0, 0]]), np.array([-1]))])
     with pytest.raises(native.FptError):
         native.fpt_hist_merge(neg)
+
+
+def test_resume_from_a_checkpoint_equals_one_run():
+    """Checkpoint / resume: a run split at id k (the checkpoint is the seed,
+    the next id and the histogram so far) and resumed over ids [k, n) gives,
+    after fpt_hist_merge, the histogram of the uninterrupted run: counts and
+    maxima exactly, sums to rounding."""
+    from paper_2206_11234_gb300 import native
+    full = W.SetSpec(**SPEC)
+    _, _, bins, counts = _run(full)
+    k = 1234
+    first = W.SetSpec(**{**SPEC, "n_traj": k})
+    rest = W.SetSpec(**{**SPEC, "n_traj": full.n_traj - k})
+    rest.traj_offset = k
+    _, _, b1, c1 = _run(first)
+    _, _, b2, c2 = _run(rest)
+    parts = np.stack([shard.pack_bins(b[:, :7], b[:, 7]) for b in (b1, b2)])
+    out, oc = native.fpt_hist_merge(parts, np.stack([c1, c2]))
+    f, c = out.numpy()[:, :7], out.numpy().view(np.int64)[:, 7]
+    assert np.array_equal(c, bins[:, 7].astype(np.int64)) and np.array_equal(f[:, 0], bins[:, 0])
+    np.testing.assert_allclose(f[:, 1:3], bins[:, 1:3], rtol=1e-12, atol=0)
+    assert np.array_equal(oc.numpy(), counts)
