@@ -280,7 +280,7 @@ def test_drift_ladder_binary32_against_binary64_every_bin(nat):
         zp = (d1[ok] / n) / sep[ok]
         allowed = int(binom.ppf(0.999, ok.sum(), 0.0027))
         paired.append((float(np.abs(zp).max()), int(np.sum(np.abs(zp) > 3)), allowed,
-                       float(np.median(sep[ok] / np.hypot(e1[ok], e2[ok]) * 0.0075))))
+                       float(np.median(sep[ok] / (np.hypot(e1[ok], e2[ok]) * 0.0075)))))
         assert np.sum(np.abs(zp) > 3) <= allowed and np.abs(zp).max() < 5, (s, paired[-1])
     print("max |P32 - P64| / combined sigma per set:", [round(w, 3) for w in worst])
     print("paired: (max |z|, bins beyond 3, allowed, paired / combined sigma) per set:", paired)
