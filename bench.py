@@ -47,9 +47,37 @@ MLP_MAC_PER_EVAL = 2 * 64 + 64 * 64 + 64
 
 
 # Sources the binary32 stepper kernel is built from: DRAM counters recorded
-# for it in profiles/ apply only while these files are unchanged.
+# for it in profiles/ apply only while their code is unchanged (the C++
+# sources are compared without comments and blank lines; build.py, which
+# holds the compiler flags, as it is).
 STEPPER_SOURCES = ("stepper.cuh", "stepper_f32.cu", "stepper_f64.cu", "stepper_types.h", "rng.cuh", "stepper_launch.h",
                    "../build.py")
+
+
+def strip_c_comments(text: str) -> str:
+    """C/C++ source without // and /* */ comments, trailing blanks and blank
+    lines (string and character literals are kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
 
 
 def stepper_source_hash() -> str:
@@ -57,8 +85,11 @@ def stepper_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2206_11234_gb300", "csrc")
     for f in STEPPER_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = fh.read()
+        if not f.endswith(".py"):
+            text = strip_c_comments(text)
+        h.update(f.encode() + b"\0" + text.encode())
     return h.hexdigest()
 
 
@@ -806,10 +837,22 @@ def main():
             dt, es = t1[0].item(), t2[1].item()
         else:
             es = tt[1].item()
+        # the link's own rate for the record copies on this machine (outside the
+        # timed loop): the part of a call that overlapping can hide
+        torch.cuda.synchronize()
+        tl = time.perf_counter()
+        for _ in range(3):
+            hN.copy_(N, non_blocking=True)
+            hl.copy_(lw, non_blocking=True)
+        torch.cuda.synchronize()
+        link_s = (time.perf_counter() - tl) / 3
         import ctypes
         h2d = ctypes.sizeof(nat.FptSet) * len(specs) + ctypes.sizeof(nat.FptParams)
         d2h = 2 * 8 * n + ctypes.sizeof(nat.FptBin) * nbins + ctypes.sizeof(nat.FptHistCounts) * len(specs)
-        e2e = {"value": es / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e = {"value": es / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_call": dt / args.steps * 1e3,
+               "records_d2h_ms": link_s * 1e3, "records_d2h_gbs": 16 * n / link_s / 1e9,
+               "copies": "records on a second stream during the histogram kernels, then bins and counters"}
 
     if rank != 0:
         if world > 1:

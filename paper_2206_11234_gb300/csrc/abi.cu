@@ -361,7 +361,7 @@ void workspace_image(const Prepared& P, const WorkspaceLayout& L, std::vector<un
 // already been copied to `ws`.
 int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L, unsigned char* ws,
                 uint64_t seed, double* out_N, double* out_logw, fpt_bin* bins, fpt_hist_counts* counts,
-                cudaStream_t stream) {
+                cudaStream_t stream, const std::function<int()>& after_stepper) {
     StepperKernel k;
     int block = 0, grid = 0;
     int rc = pick_stepper(p, P.wall, &k, &block);
@@ -380,6 +380,10 @@ int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L
     if (P.n_total > 0) {
         cudaError_t e = k.launch(a, grid, block, stream);
         if (e != cudaSuccess) return cuda_fail(e, "stepper launch");
+    }
+    if (after_stepper) {
+        rc = after_stepper();
+        if (rc) return rc;
     }
     if (bins) {
         int n_sm = 0;
@@ -405,8 +409,9 @@ int read_status(const unsigned char* ws, const WorkspaceLayout& L, cudaStream_t 
 }
 
 // One complete call: stream-ordered workspace, upload, enqueue, status, free.
+// after_stepper: as for enqueue_run.
 int run_once(const fpt_params* p, const Prepared& P, uint64_t seed, double* out_N, double* out_logw,
-             fpt_bin* bins, fpt_hist_counts* counts) {
+             fpt_bin* bins, fpt_hist_counts* counts, const std::function<int()>& after_stepper = {}) {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(p->stream);
     WorkspaceLayout L;
     workspace_layout(P, &L);
@@ -421,7 +426,7 @@ int run_once(const fpt_params* p, const Prepared& P, uint64_t seed, double* out_
     // pageable source: the copy is staged before the call returns
     e = cudaMemcpyAsync(ws, img.data(), L.bytes, cudaMemcpyHostToDevice, stream);
     int rc = (e != cudaSuccess) ? cuda_fail(e, "workspace upload") : FPT_OK;
-    if (!rc) rc = enqueue_run(p, P, L, ws, seed, out_N, out_logw, bins, counts, stream);
+    if (!rc) rc = enqueue_run(p, P, L, ws, seed, out_N, out_logw, bins, counts, stream, after_stepper);
     StepperScratch host;
     if (!rc) rc = read_status(ws, L, stream, &host);
     cudaError_t ef = cudaFreeAsync(ws, stream);
@@ -560,6 +565,26 @@ cudaError_t host_entry_pool(cudaMemPool_t* out) {
     *out = pools[dev];
     return cudaSuccess;
 }
+
+// A non-blocking stream per device for the host entry's record copies,
+// created on first use and kept for the life of the process.
+cudaError_t copy_stream(cudaStream_t* out) {
+    static std::mutex mu;
+    static std::vector<cudaStream_t> streams;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
+    if (!streams[dev]) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        streams[dev] = s;
+    }
+    *out = streams[dev];
+    return cudaSuccess;
+}
 }  // namespace
 
 int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
@@ -590,14 +615,41 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
     double* dlw = reinterpret_cast<double*>(dev + o_lw);
     fpt_bin* db = reinterpret_cast<fpt_bin*>(dev + o_bins);
     fpt_hist_counts* dc = reinterpret_cast<fpt_hist_counts*>(dev + o_cnt);
-    rc = run_once(p, P, seed, dN_, dlw, db, dc);
-    if (!rc && host_N && rec_bytes) {
-        e = cudaMemcpyAsync(host_N, dN_, rec_bytes, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "copy N to host");
+    // The records are final when the stepper ends: copy them to the host on a
+    // second stream while the histogram kernels (which only read them) run.
+    cudaStream_t side = nullptr;
+    cudaEvent_t stepper_done = nullptr, copied = nullptr;
+    e = copy_stream(&side);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&stepper_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy stream");
+    bool side_used = false;
+    if (!rc) {
+        // the side stream waits for the stepper; it is enqueued before the
+        // histogram so that the copies start as soon as the stepper ends
+        rc = run_once(p, P, seed, dN_, dlw, db, dc, [&]() -> int {
+            cudaError_t ec = cudaEventRecord(stepper_done, st);
+            if (ec != cudaSuccess) return cuda_fail(ec, "event record");
+            ec = cudaStreamWaitEvent(side, stepper_done, 0);
+            if (ec != cudaSuccess) return cuda_fail(ec, "copy stream wait");
+            side_used = true;
+            if (host_N && rec_bytes) {
+                ec = cudaMemcpyAsync(host_N, dN_, rec_bytes, cudaMemcpyDeviceToHost, side);
+                if (ec != cudaSuccess) return cuda_fail(ec, "copy N to host");
+            }
+            if (host_logw && rec_bytes) {
+                ec = cudaMemcpyAsync(host_logw, dlw, rec_bytes, cudaMemcpyDeviceToHost, side);
+                if (ec != cudaSuccess) return cuda_fail(ec, "copy logw to host");
+            }
+            return FPT_OK;
+        });
     }
-    if (!rc && host_logw && rec_bytes) {
-        e = cudaMemcpyAsync(host_logw, dlw, rec_bytes, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "copy logw to host");
+    if (side_used) {
+        // the buffers are freed on `st` only after the side stream's copies
+        cudaError_t ec = cudaEventRecord(copied, side);
+        if (ec == cudaSuccess) ec = cudaStreamWaitEvent(st, copied, 0);
+        if (!rc && ec != cudaSuccess) rc = cuda_fail(ec, "copy stream join");
+        if (ec != cudaSuccess) cudaStreamSynchronize(side);
     }
     if (!rc) {
         e = cudaMemcpyAsync(host_bins, db, bin_bytes, cudaMemcpyDeviceToHost, st);
@@ -611,6 +663,8 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
     e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "stream synchronize");
     if (!rc && ef != cudaSuccess) rc = cuda_fail(ef, "device buffers free");
+    if (stepper_done) cudaEventDestroy(stepper_done);
+    if (copied) cudaEventDestroy(copied);
     return rc;
 }
 

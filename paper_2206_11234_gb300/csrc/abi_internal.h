@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <functional>
 #include <vector>
 
 #include "fpt.h"
@@ -63,8 +64,11 @@ void clear_tuned_shapes();
 int stepper_grid(const StepperKernel& k, int block, int n_sets, unsigned long long n_total, int* grid);
 void workspace_layout(const Prepared& P, WorkspaceLayout* L);
 void workspace_image(const Prepared& P, const WorkspaceLayout& L, std::vector<unsigned char>* img);
+// Enqueues the stepper and, with bins, the histogram kernels on `stream`.
+// after_stepper (optional) is called between the two, when the records are
+// final and only read from then on; a nonzero return stops the enqueue.
 int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L, unsigned char* ws,
                 uint64_t seed, double* out_N, double* out_logw, fpt_bin* bins, fpt_hist_counts* counts,
-                cudaStream_t stream);
+                cudaStream_t stream, const std::function<int()>& after_stepper = {});
 
 }  // namespace fpt

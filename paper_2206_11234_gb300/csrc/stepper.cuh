@@ -187,26 +187,22 @@ template <>
 struct StepOf<float, FPT_MODEL_QUADRATIC> { using type = QuadPsiStep; };
 
 // Sixteen binary32 EM steps of a power model from one Philox group: as
-// steps16_f32, with the log-weight summed step by step into acc.
+// Block j (four steps, two Box–Muller pairs) of a 16-step group for the
+// power-law models: as quad_block_f32, with the log-weight summed step by step
+// into acc.
 template <int MODEL, bool WALL>
-__device__ __forceinline__ void steps16_pow(const ModelStep<float, MODEL>& model, const PhiloxLane& pl, uint32_t G,
-                                            const PhiloxKeys& keys, float twouv, float& phi, float& mn,
-                                            float& acc) {
-    uint32_t V[12];
-    philox_group(pl, G, keys, V);
+__device__ __forceinline__ void pow_block_f32(const ModelStep<float, MODEL>& model, const uint32_t V[12], int j,
+                                              float twouv, float& phi, float& mn, float& acc) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const NormalPair np = group_pair_f32(V, j, p);
-            const float q = __fmul_rn(model.kq, np.rho);
-            phi = model.advance(phi, q, np.c, acc);
-            if constexpr (WALL) phi = fminf(phi, twouv - phi);
-            const float first = phi;
-            phi = model.advance(phi, q, np.s, acc);
-            if constexpr (WALL) phi = fminf(phi, twouv - phi);
-            mn = min3f(mn, first, phi);
-        }
+    for (int p = 0; p < 2; ++p) {
+        const NormalPair np = group_pair_f32(V, j, p);
+        const float q = __fmul_rn(model.kq, np.rho);
+        phi = model.advance(phi, q, np.c, acc);
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        const float first = phi;
+        phi = model.advance(phi, q, np.s, acc);
+        if constexpr (WALL) phi = fminf(phi, twouv - phi);
+        mn = min3f(mn, first, phi);
     }
 }
 
@@ -218,27 +214,48 @@ __device__ __forceinline__ float step1_f32(const Step& model, float phi, float t
     return phi;
 }
 
-// Sixteen binary32 EM steps from one Philox group (three Philox blocks, eight
-// Box–Muller pairs): the state update, the wall, the block minimum (one
-// three-way minimum per pair) and the running sum of
-// rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
+// Block j (four steps, two Box–Muller pairs) of a 16-step group's words V:
+// the state update, the wall, the block minimum (one three-way minimum per
+// pair) and the running sum of rho (c + s) = -(xi0 + xi1) / sqrt(2 ln 2).
 template <bool WALL, typename Step>
-__device__ __forceinline__ void steps16_f32(const Step& model, const PhiloxLane& pl, uint32_t G,
-                                            const PhiloxKeys& keys, float twouv, float& phi, float& mn,
-                                            float& srho) {
+__device__ __forceinline__ void quad_block_f32(const Step& model, const uint32_t V[12], int j, float twouv,
+                                               float& phi, float& mn, float& srho) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const NormalPair np = group_pair_f32(V, j, p);
+        const float q = __fmul_rn(model.kq, np.rho);
+        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.c, model.tc), twouv);
+        const float first = phi;
+        phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.s, model.tc), twouv);
+        mn = min3f(mn, first, phi);
+        srho = __fmaf_rn(np.rho, np.c + np.s, srho);
+    }
+}
+
+// KS binary32 steps: Philox groups G0 .. G0 + KS/16 - 1, each three Philox
+// blocks and four Box–Muller blocks block(V, j), j = 0..3.  Software-pipelined:
+// the Philox blocks of group g + 1 are computed between the Box–Muller blocks
+// of group g, so that a warp's instruction stream interleaves the integer
+// multiplies with the XU work instead of alternating between the two phases.
+// The words, and so the results, are those of computing each group in turn.
+template <int KS, typename Block>
+__device__ __forceinline__ void pipelined_groups(const PhiloxLane& pl, uint32_t G0, const PhiloxKeys& keys,
+                                                 Block&& block) {
+    static_assert(KS % 16 == 0, "whole 16-step groups");
     uint32_t V[12];
-    philox_group(pl, G, keys, V);
+    philox_group(pl, G0, keys, V);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int g = 0; g < KS / 16; ++g) {
+        uint32_t Vn[12];
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const NormalPair np = group_pair_f32(V, j, p);
-            const float q = __fmul_rn(model.kq, np.rho);
-            phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.c, model.tc), twouv);
-            const float first = phi;
-            phi = step1_f32<WALL>(model, phi, __fmaf_rn(q, np.s, model.tc), twouv);
-            mn = min3f(mn, first, phi);
-            srho = __fmaf_rn(np.rho, np.c + np.s, srho);
+        for (int j = 0; j < 4; ++j) {
+            if (g + 1 < KS / 16 && j < 3)
+                philox_block(pl, 3u * (G0 + (uint32_t)g + 1u) + (uint32_t)j, keys, Vn + 4 * j);
+            block(V, j);
+        }
+        if (g + 1 < KS / 16) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) V[i] = Vn[i];
         }
     }
 }
@@ -564,11 +581,12 @@ __device__ __forceinline__ void replay_batch(const Pending<Real, PREC>* q, int c
 // ---------------------------------------------------------------------------
 // Register cap per thread.  64 is the largest that keeps 32 warps resident per
 // SM (4 blocks of 256 or 2 of 512 threads: 65,536 registers), and its spare
-// registers let the compiler overlap a block's Philox words with the previous
-// block's Box-Muller and updates.  Measured on the drift-dominated ladder
-// (steps/s of the kernel, 256 / 512 threads): 56: 1.137 / 1.140e12,
-// 64: 1.152 / 1.155e12, 72: 1.145 / 1.116e12 (fewer resident warps); 40 and
-// 48 (more warps) were no faster than 56.  At 64 the quadratic, constant and
+// registers hold the next group's Philox words while the current group's
+// Box-Muller blocks run.  Measured on the drift-dominated ladder (steps/s of
+// the kernel, 64-step blocks): 64 registers, 512 threads (32 warps per SM):
+// 1.335e12; 56 registers, 384 threads (36 warps): 1.325e12; 48 registers,
+// 256 threads (40 warps): 1.313e12 -- more resident warps do not pay for the
+// spills they need.  At 64 the quadratic, constant and
 // power-law kernels are spill-free; the polynomial-potential ones (eight
 // coefficients per set) spill 12-48 bytes (56-84 at a cap of 56).  The binary64
 // reference kernels are built with a larger cap.
@@ -677,13 +695,14 @@ stepper_kernel(const StepperParams P) {
         Real sblk = (Real)0;
         if constexpr (sizeof(Real) == 4) {
             const uint32_t G0 = (uint32_t)m0 >> 4;
-#pragma unroll
-            for (int g = 0; g < KS / 16; ++g) {
-                if constexpr (is_pow_model(MODEL))
-                    steps16_pow<MODEL, WALL>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
-                else
-                    steps16_f32<WALL>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, sblk);
-            }
+            if constexpr (is_pow_model(MODEL))
+                pipelined_groups<KS>(pl, G0, P.keys, [&](const uint32_t* V, int j) {
+                    pow_block_f32<MODEL, WALL>(model, V, j, twouv, phi, mn, sblk);
+                });
+            else
+                pipelined_groups<KS>(pl, G0, P.keys, [&](const uint32_t* V, int j) {
+                    quad_block_f32<WALL>(model, V, j, twouv, phi, mn, sblk);
+                });
         } else {
             const uint32_t k0 = (uint32_t)m0 >> 2;
 #pragma unroll

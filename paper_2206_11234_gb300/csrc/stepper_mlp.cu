@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams
         const int m0 = m;
         float mn = phi, srho = 0.f;
         const uint32_t G0 = (uint32_t)m0 >> 4;
-#pragma unroll
-        for (int g = 0; g < KS / 16; ++g)
-            steps16_f32<true>(model, pl, G0 + (uint32_t)g, P.keys, twouv, phi, mn, srho);
+        pipelined_groups<KS>(pl, G0, P.keys, [&](const uint32_t* V, int j) {
+            quad_block_f32<true>(model, V, j, twouv, phi, mn, srho);
+        });
         const float sblk = -kSqrt2Ln2 * srho;  // the block's sum of normals
         m = m0 + KS;
         const bool event = live && (mn <= phi_end || m >= m_max);

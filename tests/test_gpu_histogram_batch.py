@@ -148,6 +148,21 @@ def test_host_entry_matches_device_entry(nat):
     fh, ch = nat.bins_to_numpy(hb)
     assert np.array_equal(cb, ch) and np.array_equal(fb[:, 0], fh[:, 0])
     np.testing.assert_allclose(fh[:, 1:], fb[:, 1:], rtol=1e-12, atol=1e-300)
+    # the records are copied on a second stream while the histogram runs: the
+    # same results with pageable record buffers, and on a caller's stream
+    for pinned, on_stream in ((False, False), (True, True)):
+        hN2 = torch.full((n,), -1.0, dtype=torch.float64)
+        hl2 = torch.full((n,), -1.0, dtype=torch.float64)
+        if pinned:
+            hN2, hl2 = hN2.pin_memory(), hl2.pin_memory()
+        hb2, hc2 = torch.empty_like(hb), torch.empty_like(hc)
+        s = torch.cuda.Stream() if on_stream else None
+        p2 = nat.make_params(precision=wl.precision, m=s0.m, n_max=s0.n_max, stream=s)
+        nat.fpt_simulate_batch_host(p2, sets, wl.seed, hN2, hl2, hb2, hc2)
+        assert torch.equal(hN2, hN) and torch.equal(hl2, hl) and torch.equal(hc2, hc)
+        fh2, ch2 = nat.bins_to_numpy(hb2)
+        assert np.array_equal(ch2, ch) and np.array_equal(fh2[:, 0], fh[:, 0])
+        np.testing.assert_allclose(fh2[:, 1:], fh[:, 1:], rtol=1e-12, atol=1e-300)
 
 
 def test_invalid_arguments_are_rejected_before_launch(nat):
