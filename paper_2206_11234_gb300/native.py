@@ -546,9 +546,11 @@ def estimates_to_dict(est: torch.Tensor) -> dict:
     return {f: a[:, i].copy() for i, f in enumerate(ESTIMATE_FIELDS)}
 
 
-def lognormal_applies(est: dict, threshold: float = 0.005, min_count: int = 8) -> bool:
+def lognormal_applies(est: dict, threshold: float = 0.005, min_count: int = 400) -> bool:
     """The rule of §2.4: the lognormal estimate is used when no bin's normality
-    p-value (bins with >= min_count runs) falls below the threshold (0.5 %)."""
+    p-value falls below the threshold (0.5 %).  The bins tested are those the
+    histogram keeps, >= min_count runs (§2.1 truncates bins below 400 runs);
+    the test itself needs 8."""
     import numpy as np
     p = est["p_normal"][est["count"] >= min_count]
     p = p[np.isfinite(p)]

@@ -117,6 +117,9 @@ def test_lognormal_rule_on_simulated_runs(nat):
     assert big.sum() >= 10
     p = got["p_normal"][big]
     assert np.median(p) > 0.05 and np.mean(p < 0.005) <= 0.1, p
+    # the rule over the kept bins accepts the lognormal estimate here, while a
+    # bin of a few dozen runs alone can refuse it
+    assert nat.lognormal_applies(got)
     d = np.abs(got["p_lognormal"][big] - got["p_direct"][big])
     err = np.hypot(np.maximum(got["eps_lo"][big], got["eps_hi"][big]), got["se_direct"][big])
     assert np.mean(d <= 3 * err) >= 0.9
