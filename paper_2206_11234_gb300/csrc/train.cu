@@ -36,6 +36,7 @@ struct TailAcc {
     unsigned long long max_key;  // ordered key of the largest ln w in the tail
     double s1, s2;               // sum exp(lw - max), sum exp(2 (lw - max)) over the tail
     unsigned long long count;    // runs in the tail
+    unsigned long long n_rows;   // rows written by records_to_rows
 };
 
 __device__ __forceinline__ bool in_tail(double N, double tail_N) {
@@ -87,17 +88,41 @@ __global__ void tail_sums(const double* __restrict__ N, const double* __restrict
     }
 }
 
-// rows of the batched MLP backward: inputs of block k and g_k = (c_run / sum c) (-sqrt(dN) Xi_k)
+// Rows of the batched MLP backward: inputs of block k and
+// g_k = (c_run / sum c) (-sqrt(dN) Xi_k), for the blocks of runs with c != 0
+// only.  The others (runs outside the tail, or whose w^2 underflows) have
+// g_k = 0 exactly and add nothing to the gradient, so they are left out: the
+// rows are compacted, one atomic per warp, in no particular order (the
+// backward's sums do not depend on it beyond rounding).  acc->n_rows counts
+// them.
 __global__ void records_to_rows(const fpt_mlp_record* __restrict__ rec, long long n_rec,
-                                const double* __restrict__ coef, const TailAcc* acc, double sq,
+                                const double* __restrict__ coef, TailAcc* acc, double sq,
                                 float* __restrict__ phi, float* __restrict__ Nin, float* __restrict__ g) {
     const double inv = acc->s2 > 0.0 ? 1.0 / acc->s2 : 0.0;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rec;
-         r += (long long)gridDim.x * blockDim.x) {
-        const fpt_mlp_record x = rec[r];
-        phi[r] = x.phi;
-        Nin[r] = x.N;
-        g[r] = (float)(coef[x.run] * inv * (-sq * (double)x.xi_sum));
+    const unsigned lane = threadIdx.x & 31u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // warp-uniform loop: every lane of a warp runs the same iterations
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); base < n_rec;
+         base += stride) {
+        const long long r = base + lane;
+        fpt_mlp_record x{};
+        double c = 0.0;
+        if (r < n_rec) {
+            x = rec[r];
+            c = coef[x.run];
+        }
+        const bool keep = c != 0.0;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m == 0u) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(&acc->n_rows, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (keep) {
+            const long long o = (long long)at + __popc(m & ((1u << lane) - 1u));
+            phi[o] = x.phi;
+            Nin[o] = x.N;
+            g[o] = (float)(c * inv * (-sq * (double)x.xi_sum));
+        }
     }
 }
 
@@ -162,10 +187,19 @@ extern "C" int fpt_mlp_train_step(const fpt_params* p, const fpt_set* set, uint6
         if (e != cudaSuccess) rc = cuda_fail(e, "training kernels");
         if (!rc) e = cudaMemsetAsync(S->grad, 0, sizeof(float) * FPT_MLP_NPARAM, st);
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "gradient clear");
-        if (!rc) rc = fpt_mlp_backward(S->w, rphi, rN, rg, n_rec, S->grad, p->stream);
     }
+    // the tail sums and the number of rows (the backward's size) on the host
     TailAcc h;
     std::memset(&h, 0, sizeof(h));
+    if (!rc) {
+        e = cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "tail sums");
+    }
+    if (!rc && h.n_rows > (unsigned long long)n_rec) rc = fail(FPT_ECUDA, "%llu rows from %lld records", h.n_rows, (long long)n_rec);
+    if (!rc && h.n_rows > 0)
+        rc = fpt_mlp_backward(S->w, S->rows, S->rows + S->record_capacity, S->rows + 2 * S->record_capacity,
+                              (int64_t)h.n_rows, S->grad, p->stream);
     if (!rc) {
         S->step += 1;
         const float b1 = 0.9f, b2 = 0.999f;
@@ -174,7 +208,6 @@ extern "C" int fpt_mlp_train_step(const fpt_params* p, const fpt_set* set, uint6
                                                                  FPT_MLP_NPARAM, (float)lr, b1, b2, 1e-8f, c1, c2,
                                                                  S->w);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "Adam update");
     }
