@@ -121,8 +121,9 @@ def parse():
     ap.add_argument("--workload", default="drift_ladder",
                     choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall",
                              "learned_bias", "estimators", "power_bias", "multi_bias"])
-    ap.add_argument("--train-steps", type=int, default=256, help="learned_bias: Adam steps")
-    ap.add_argument("--lr", type=float, default=2e-3, help="learned_bias: Adam learning rate")
+    ap.add_argument("--train-steps", type=int, default=2048, help="learned_bias: Adam steps")
+    ap.add_argument("--train-runs", type=int, default=1 << 14, help="learned_bias: runs per Adam step")
+    ap.add_argument("--lr", type=float, default=3e-3, help="learned_bias: Adam learning rate")
     ap.add_argument("--k-eval", type=int, default=64, choices=(16, 32, 64, 128),
                     help="learned_bias: steps between two evaluations of the bias network")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's runs")
@@ -260,7 +261,7 @@ def learned_bias_experiment(args, rates=None):
     N > 40, censored at N = 60.  A ladder of constant b (2^20 runs each) picks
     the best b by effective samples per EM step; that b is rerun on as many
     runs as the learned inference (2^26) for a like-for-like n_eff/s.  Training:
-    2^16 runs per Adam step, --train-steps steps (2^24 runs at the default),
+    --train-runs runs per Adam step (2^14), --train-steps steps (2048: 2^25 runs),
     timed on the host clock around the device-synchronised loop.  Everything
     is scaled by --scale.  The FP64 oracle runs the trained network on a
     bounded sample as a cross-check of the estimate.  Returns a dict."""
@@ -309,7 +310,7 @@ def learned_bias_experiment(args, rates=None):
     with ClockSampler(0) as clk_c:
         best = constant(best_b, n_i, 13)
     # training, starting from the best constant amplitude
-    n_t = max(1024, int((1 << 16) * args.scale))
+    n_t = max(1024, int(args.train_runs * args.scale))
     init = W.mlp_params(seed=5, gain=1.0, out_scale=0.05)
     init[-1] = best_b
     norm = (5.2, 0.5, 30.0, 1.0 / 15.0)
