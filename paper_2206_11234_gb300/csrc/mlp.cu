@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const fpt_mlp_params* 
 }
 
 struct MlpBwdSmem {
-    MlpFwdSmem f;                                   // A = h1 (rows r, K = k), W2 (rows n, K = k)
+    MlpTile f;                                      // A = h1 (rows r, K = k), W2 (rows n, K = k)
     alignas(128) unsigned char W2T[64 * 64 * 2];    // rows k, K = n
     alignas(128) unsigned char D2[kTileBytes64];    // delta2: rows r, K = n
     alignas(128) unsigned char D2T[128 * 128 * 2];  // delta2^T: rows n (64..127 zero), K = r
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
                                                            unsigned* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char s_raw[];
     MlpBwdSmem& B = *reinterpret_cast<MlpBwdSmem*>(s_raw);
-    MlpFwdSmem& S = B.f;
+    MlpTile& S = B.f;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
         B.gb1[j] = B.gb2[j] = B.gw3[j] = 0.f;
     }
     if (tid == 0) B.gb3 = 0.f;
-    mlp_fwd_load(S, P);  // fences the generic writes above and synchronises
+    mlp_tile_load(S, P);  // fences the generic writes above and synchronises
     tc::fence_after_sync();
     uint32_t phase = 0;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;

@@ -4,8 +4,8 @@
 // blocks of KS steps without per-step branches, a per-warp queue of finished
 // runs replayed 32 at a time, refills from a ticket counter), with one CTA of
 // 128 threads = one tensor-core tile: at the start of every block all 128
-// lanes evaluate b at their own (phi, N elapsed) in one tcgen05 MMA tile and
-// hold it for the block.  With B = b S the weight term of a step is
+// lanes evaluate b at their own (phi, N elapsed) (mlp.cuh: one tcgen05 MMA for
+// the hidden layer, the rest on the CUDA cores) and hold it for the block.  With B = b S the weight term of a step is
 // -(b xi sqrt(dN) + b^2 dN / 2) (arXiv:2206.11234 §2.2 Eqs. (12)-(14)), so a
 // block adds -b sqrt(dN) Xi - b^2 n dN / 2 with Xi its sum of normals and n
 // its steps; the running ln w is kept in binary64.
@@ -126,11 +126,12 @@ __device__ __forceinline__ void replay_mlp(const PendingMlp* q, int cnt, const S
     my_steps += (unsigned long long)M;
 }
 
-// The bound caps the kernel at 64 registers (63 used, 16 bytes spilled; 72
-// without it).  Residency stays at 5 CTAs per SM, set by the 44 KB of shared
-// memory each holds (operand tiles and replay queues), but the schedule the
-// compiler finds under the cap waits less on dependencies: 6.93e11 against
-// 6.80e11 steps/s on the learned-bias workload.
+// The bound caps the kernel at 64 registers (16 bytes spilled; 72 without
+// it), for a schedule that waits less on dependencies (6.93e11 against
+// 6.80e11 steps/s on the learned-bias workload when measured).  Residency is
+// 6 CTAs per SM, set by the ~34.5 KB of shared memory each holds (the tile's
+// 26 KB of operands and parameters and 8 KB of replay queues); at 5 CTAs,
+// with the earlier three-MMA tile of 44 KB, the kernel ran at the same speed.
 template <int KS>
 __global__ void __launch_bounds__(128, 8) stepper_mlp_kernel(const StepperParams P, const fpt_mlp_params* __restrict__ W,
                                                           const RecordSink sink) {
