@@ -74,6 +74,28 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sums of v[0..15] over the 32 lanes of the warp, 16 at once: at each step a
+// lane keeps one half of its values (the upper half when its lane bit is set)
+// and adds its partner's copy of that half, so the values carried halve while
+// the lanes summed double.  Returns in lane L the sum of index L >> 1 (lanes
+// 2u and 2u + 1 both hold index u).  16 shuffles for 16 sums instead of 80.
+// v is overwritten.
+__device__ __forceinline__ float warp_sum16(float v[16]) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int step = 0; step < 4; ++step) {
+        const int o = 16 >> step, h = 8 >> step;
+        const bool up = (lane & (unsigned)o) != 0u;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 __device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
 }
@@ -137,28 +159,30 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
             tc::tmem_ld16(S.tmem + lane_base + 16 * c, z);
             tc::tmem_wait_ld();
             uint32_t q[8];
+            float dd[16], gh[16];
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
-                float d[2];
                 const int n0 = 16 * c + e;
                 const uint32_t hh = tc::tanh_bf16x2(tc::pack_bf16(z[e] + S.b2[n0], z[e + 1] + S.b2[n0 + 1]));
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int nn = n0 + u;
                     const float h2 = u == 0 ? tc::bf16_lo(hh) : tc::bf16_hi(hh);
-                    d[u] = gi * S.w3[nn] * (1.f - h2 * h2);
-                    store_bf16(B.D2T, tc::kmajor_offset(nn, tid, 128), d[u]);
-                    const float sw3 = warp_sum(gi * h2);
-                    const float sb2 = warp_sum(d[u]);
-                    if (lane == 0) {
-                        atomicAdd(&B.gw3[nn], sw3);
-                        atomicAdd(&B.gb2[nn], sb2);
-                    }
+                    dd[e + u] = gi * S.w3[nn] * (1.f - h2 * h2);
+                    gh[e + u] = gi * h2;
+                    store_bf16(B.D2T, tc::kmajor_offset(nn, tid, 128), dd[e + u]);
                 }
-                q[e / 2] = tc::pack_bf16(d[0], d[1]);
+                q[e / 2] = tc::pack_bf16(dd[e], dd[e + 1]);
             }
             *reinterpret_cast<uint4*>(B.D2 + tc::kmajor_offset(tid, 16 * c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
             *reinterpret_cast<uint4*>(B.D2 + tc::kmajor_offset(tid, 16 * c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+            // dw3 += g h2, db2 += delta2, summed over the warp's rows
+            const float sw3 = warp_sum16(gh);
+            const float sb2 = warp_sum16(dd);
+            if ((lane & 1u) == 0u) {
+                atomicAdd(&B.gw3[16 * c + (lane >> 1)], sw3);
+                atomicAdd(&B.gb2[16 * c + (lane >> 1)], sb2);
+            }
         }
         const float sg = warp_sum(gi);
         if (lane == 0) atomicAdd(&B.gb3, sg);
@@ -188,18 +212,24 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(const fpt_mlp_params*
             float dh[16];
             tc::tmem_ld16(S.tmem + lane_base + 16 * c, dh);
             tc::tmem_wait_ld();
+            float d0[16], d1x0[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int k = 16 * c + e;
                 const uint16_t hb = *reinterpret_cast<const uint16_t*>(S.A + tc::kmajor_offset(tid, k, 64));
                 const float h1 = __uint_as_float((uint32_t)hb << 16);
                 const float d1 = dh[e] * (1.f - h1 * h1);
-                const float s0 = warp_sum(d1), s1 = warp_sum(d1 * x0), s2 = warp_sum(d1 * x1);
-                if (lane == 0) {
-                    atomicAdd(&B.gb1[k], s0);
-                    atomicAdd(&B.gw1[k][0], s1);
-                    atomicAdd(&B.gw1[k][1], s2);
-                }
+                d0[e] = d1;
+                d1x0[e] = d1 * x0;
+                dh[e] = d1 * x1;  // dh is dead after this element: reuse it for d1 x1
+            }
+            // db1 += delta1, dW1 += delta1 x^T, summed over the warp's rows
+            const float s0 = warp_sum16(d0), s1 = warp_sum16(d1x0), s2 = warp_sum16(dh);
+            if ((lane & 1u) == 0u) {
+                const int k = 16 * c + (int)(lane >> 1);
+                atomicAdd(&B.gb1[k], s0);
+                atomicAdd(&B.gw1[k][0], s1);
+                atomicAdd(&B.gw1[k][1], s2);
             }
         }
         tc::fence_before_sync();
