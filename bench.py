@@ -121,7 +121,7 @@ def parse():
     ap.add_argument("--workload", default="drift_ladder",
                     choices=["drift_ladder", "quadratic_b1", "batched_uneven", "diffusion_wall",
                              "learned_bias", "estimators", "power_bias", "multi_bias"])
-    ap.add_argument("--train-steps", type=int, default=2048, help="learned_bias: Adam steps")
+    ap.add_argument("--train-steps", type=int, default=4096, help="learned_bias: Adam steps")
     ap.add_argument("--train-runs", type=int, default=1 << 14, help="learned_bias: runs per Adam step")
     ap.add_argument("--lr", type=float, default=3e-3, help="learned_bias: Adam learning rate")
     ap.add_argument("--k-eval", type=int, default=64, choices=(16, 32, 64, 128),
@@ -261,7 +261,7 @@ def learned_bias_experiment(args, rates=None):
     N > 40, censored at N = 60.  A ladder of constant b (2^20 runs each) picks
     the best b by effective samples per EM step; that b is rerun on as many
     runs as the learned inference (2^26) for a like-for-like n_eff/s.  Training:
-    --train-runs runs per Adam step (2^14), --train-steps steps (2048: 2^25 runs),
+    --train-runs runs per Adam step (2^14), --train-steps steps (4096: 2^26 runs),
     timed on the host clock around the device-synchronised loop.  Everything
     is scaled by --scale.  The FP64 oracle runs the trained network on a
     bounded sample as a cross-check of the estimate.  Returns a dict."""
