@@ -60,6 +60,49 @@ cudaError_t lib_malloc_from_pool_async(void** p, size_t bytes, cudaMemPool_t poo
     return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
+// The library's stream-ordered memory pool, one per device, created on first
+// use, for the allocations made afresh at every call (call workspaces, the
+// host-buffer entry's device buffers).  Its release threshold is the maximum,
+// so what one call frees stays mapped for the next; the default pool returns
+// memory to the system at every synchronisation, and mapping tens or hundreds
+// of megabytes again costs milliseconds per call.
+cudaError_t library_pool(cudaMemPool_t* out) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t lib_malloc_retained_async(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool;
+    cudaError_t e = library_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return lib_malloc_from_pool_async(p, bytes, pool, st);
+}
+
 cudaError_t lib_malloc(void** p, size_t bytes) {
     if (take_alloc_failure()) {
         *p = nullptr;
@@ -349,6 +392,8 @@ void workspace_layout(const Prepared& P, WorkspaceLayout* L) {
     L->off_sets = align_up(sizeof(StepperScratch), 256);
     L->off_segs = align_up(L->off_sets + P.sets.size() * sizeof(SetConst), 256);
     L->bytes = align_up(L->off_segs + P.segs.size() * sizeof(HistSeg), 256);
+    L->off_bin_idx = L->bytes;
+    L->total = P.segs.empty() ? L->bytes : L->bytes + align_up((size_t)P.n_total * sizeof(int), 256);
 }
 
 void workspace_image(const Prepared& P, const WorkspaceLayout& L, std::vector<unsigned char>* img) {
@@ -390,8 +435,10 @@ int enqueue_run(const fpt_params* p, const Prepared& P, const WorkspaceLayout& L
         rc = device_sm_count(&n_sm);
         if (rc) return rc;
         unsigned* status = reinterpret_cast<unsigned*>(ws + L.off_scratch + offsetof(StepperScratch, status));
+        int* bin_idx = L.total > L.bytes ? reinterpret_cast<int*>(ws + L.off_bin_idx) : nullptr;
         cudaError_t e = hist_launch(reinterpret_cast<const HistSeg*>(ws + L.off_segs), (int)P.segs.size(),
-                                    P.max_nb, P.max_n, out_N, out_logw, bins, counts, n_sm, stream, status);
+                                    P.max_nb, P.max_n, out_N, out_logw, bins, counts, n_sm, stream, status,
+                                    bin_idx);
         if (e != cudaSuccess) return cuda_fail(e, "histogram launch");
     }
     return FPT_OK;
@@ -421,7 +468,7 @@ int run_once(const fpt_params* p, const Prepared& P, uint64_t seed, double* out_
     const unsigned injected = take_injected_status();
     std::memcpy(img.data() + L.off_scratch + offsetof(StepperScratch, status), &injected, sizeof(injected));
     unsigned char* ws = nullptr;
-    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&ws), L.bytes, stream);
+    cudaError_t e = lib_malloc_retained_async(reinterpret_cast<void**>(&ws), L.total, stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     // pageable source: the copy is staged before the call returns
     e = cudaMemcpyAsync(ws, img.data(), L.bytes, cudaMemcpyHostToDevice, stream);
@@ -498,21 +545,25 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
     h.n_bins = n_bins;
     h.n_sub = n_sub;
     h.bin0 = 0;
-    // workspace: the segment, then the status word (zero)
+    // workspace: the segment, then the status word (zero), then (not uploaded)
+    // one int per record for the bin index of pass 1
     struct HistWork {
         HistSeg seg;
         unsigned status;
     } hw{};
     hw.seg = h;
+    const size_t off_idx = align_up(sizeof(HistWork), 256);
     HistWork* d_w = nullptr;
-    cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&d_w), sizeof(HistWork), st);
+    cudaError_t e = lib_malloc_retained_async(reinterpret_cast<void**>(&d_w), off_idx + (size_t)n * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "histogram workspace");
+    int* bin_idx = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(d_w) + off_idx);
     e = cudaMemcpyAsync(d_w, &hw, sizeof(HistWork), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "histogram upload");
     int n_sm = 0;
     if (!rc) rc = device_sm_count(&n_sm);
     if (!rc) {
-        e = hist_launch(&d_w->seg, 1, n_bins * n_sub, n, N, logw, bins, counts, n_sm, st, &d_w->status);
+        e = hist_launch(&d_w->seg, 1, n_bins * n_sub, n, N, logw, bins, counts, n_sm, st, &d_w->status,
+                        bin_idx);
         if (e != cudaSuccess) rc = cuda_fail(e, "histogram launch");
     }
     unsigned status = 0u;
@@ -531,40 +582,6 @@ int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins
 }
 
 namespace {
-// Stream-ordered memory pool of the host-buffer entry, one per device, created
-// on first use.  Its release threshold is the maximum, so the device buffers
-// one call frees stay mapped for the next; the default pool returns them to
-// the system at every synchronisation, and mapping hundreds of megabytes
-// again costs milliseconds per call.
-cudaError_t host_entry_pool(cudaMemPool_t* out) {
-    static std::mutex mu;
-    static std::vector<cudaMemPool_t> pools;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
-    if (!pools[dev]) {
-        cudaMemPoolProps props;
-        std::memset(&props, 0, sizeof(props));
-        props.allocType = cudaMemAllocationTypePinned;
-        props.handleTypes = cudaMemHandleTypeNone;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = dev;
-        cudaMemPool_t pool;
-        e = cudaMemPoolCreate(&pool, &props);
-        if (e != cudaSuccess) return e;
-        uint64_t keep = ~0ull;
-        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        if (e != cudaSuccess) {
-            cudaMemPoolDestroy(pool);
-            return e;
-        }
-        pools[dev] = pool;
-    }
-    *out = pools[dev];
-    return cudaSuccess;
-}
 
 // A non-blocking stream per device for the host entry's record copies,
 // created on first use and kept for the life of the process.
@@ -607,7 +624,7 @@ int fpt_simulate_batch_host(const fpt_params* p, const fpt_set* sets, int32_t n_
     const size_t o_cnt = o_bins + (bin_bytes + 255) / 256 * 256;
     const size_t total = o_cnt + cnt_bytes;
     cudaMemPool_t pool;
-    cudaError_t e = host_entry_pool(&pool);
+    cudaError_t e = library_pool(&pool);
     if (e != cudaSuccess) return cuda_fail(e, "memory pool");
     e = lib_malloc_from_pool_async(reinterpret_cast<void**>(&dev), total, pool, st);
     if (e != cudaSuccess) return cuda_fail(e, "device buffers");

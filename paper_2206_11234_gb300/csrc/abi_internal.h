@@ -17,6 +17,9 @@ namespace fpt {
 // cudaErrorMemoryAllocation without allocating, as a full device would.
 cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st);
 cudaError_t lib_malloc_from_pool_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st);
+// From the library's pool, which keeps freed memory mapped (per device).
+cudaError_t library_pool(cudaMemPool_t* out);
+cudaError_t lib_malloc_retained_async(void** p, size_t bytes, cudaStream_t st);
 cudaError_t lib_malloc(void** p, size_t bytes);
 // Status bits to pre-set in the next uploaded stepper scratch (fpt_inject_status), consumed.
 unsigned take_injected_status();
@@ -51,8 +54,12 @@ struct Prepared {
     long long total_bins;
 };
 
+// bytes: the part uploaded from the host image (scratch, set table, histogram
+// segments); total: bytes plus, with histograms, a region that is not
+// uploaded: one int per record (the bin index of histogram pass 1).
 struct WorkspaceLayout {
     size_t off_scratch, off_sets, off_segs, bytes;
+    size_t off_bin_idx, total;
 };
 
 int prepare(const fpt_params* p, const fpt_set* sets, int n_sets, bool with_hist, Prepared* P);

@@ -78,7 +78,8 @@ __global__ void hist_init(const HistSeg* __restrict__ segs, int n_segs, fpt_bin*
 
 __global__ void hist_pass_max(const double* __restrict__ N, const double* __restrict__ lw,
                               const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins,
-                              fpt_hist_counts* __restrict__ counts, unsigned* status) {
+                              fpt_hist_counts* __restrict__ counts, unsigned* status,
+                              int* __restrict__ bin_idx) {
     extern __shared__ unsigned long long s_key[];
     const HistSeg h = segs[blockIdx.y];
     const int nb = h.n_bins * h.n_sub;
@@ -100,6 +101,7 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
             over += (cat == 2);
             cens += (cat == 3);
             if (cat == 0) key = ord_key(lw[r]);
+            if (bin_idx) bin_idx[r] = bin;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, bin);
         // the group leader (lowest lane of the bin) takes the max over its peers,
@@ -133,7 +135,8 @@ __global__ void hist_pass_max(const double* __restrict__ N, const double* __rest
 }
 
 __global__ void hist_pass_sum(const double* __restrict__ N, const double* __restrict__ lw,
-                              const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins, unsigned* status) {
+                              const HistSeg* __restrict__ segs, fpt_bin* __restrict__ bins, unsigned* status,
+                              const int* __restrict__ bin_idx) {
     extern __shared__ double s_acc[];  // [nb][kSums] sums, then [nb] counts
     const HistSeg h = segs[blockIdx.y];
     const int nb = h.n_bins * h.n_sub;
@@ -150,7 +153,11 @@ __global__ void hist_pass_sum(const double* __restrict__ N, const double* __rest
         double v[kSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (i < h.n) {
             const long long r = h.first + i;
-            if (classify(N[r], h, h.id_offset + (unsigned long long)i, bin, status) == 0) {
+            if (bin_idx)
+                bin = bin_idx[r];
+            else if (classify(N[r], h, h.id_offset + (unsigned long long)i, bin, status) != 0)
+                bin = -1;
+            if (bin >= 0) {
                 const unsigned long long k =
                     (unsigned long long)__double_as_longlong(bins[h.bin0 + bin].max_lw);
                 const double x = lw[r] - ord_value(k);
@@ -215,7 +222,7 @@ size_t hist_smem_bytes(int max_nb) { return (size_t)max_nb * (kSums * sizeof(dou
 
 cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long max_n,
                         const double* N, const double* lw, fpt_bin* bins, fpt_hist_counts* counts,
-                        int n_sm, cudaStream_t stream, unsigned* status) {
+                        int n_sm, cudaStream_t stream, unsigned* status, int* bin_idx) {
     const size_t smem_sum = hist_smem_bytes(max_nb);
     const size_t smem_max = (size_t)max_nb * sizeof(unsigned long long);
     // opt in to large dynamic shared memory (per device; cheap to repeat)
@@ -235,10 +242,11 @@ cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long
     int per_seg = (int)(want < 1 ? 1 : want);
     const int cap = (2 * n_sm + n_segs - 1) / n_segs;
     if (per_seg > cap) per_seg = cap < 1 ? 1 : cap;
-    hist_pass_max<<<dim3(per_seg, n_segs), threads, smem_max, stream>>>(N, lw, d_segs, bins, counts, status);
+    hist_pass_max<<<dim3(per_seg, n_segs), threads, smem_max, stream>>>(N, lw, d_segs, bins, counts, status,
+                                                                        bin_idx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    hist_pass_sum<<<dim3(per_seg, n_segs), threads, smem_sum, stream>>>(N, lw, d_segs, bins, status);
+    hist_pass_sum<<<dim3(per_seg, n_segs), threads, smem_sum, stream>>>(N, lw, d_segs, bins, status, bin_idx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     hist_final<<<dim3(init_blocks, n_segs), threads, 0, stream>>>(d_segs, bins);

@@ -22,8 +22,11 @@ size_t hist_smem_bytes(int max_nb);
 // Enqueue the four histogram kernels for n_segs segments (device array
 // d_segs).  max_nb = max over segments of n_bins * n_sub, max_n = max records.
 // status: device status word (nullable), written only by FPT_DEBUG checks.
+// bin_idx (nullable): one int per record, indexed like N; pass 1 stores each
+// record's bin there (-1 outside the range) and pass 2 reads it instead of
+// classifying the record again.
 cudaError_t hist_launch(const HistSeg* d_segs, int n_segs, int max_nb, long long max_n,
                         const double* N, const double* lw, fpt_bin* bins, fpt_hist_counts* counts,
-                        int n_sm, cudaStream_t stream, unsigned* status);
+                        int n_sm, cudaStream_t stream, unsigned* status, int* bin_idx = nullptr);
 
 }  // namespace fpt

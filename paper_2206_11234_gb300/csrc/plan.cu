@@ -65,7 +65,7 @@ extern "C" int fpt_plan_create(const fpt_params* p, const fpt_set* sets, int32_t
     if (!rc) {
         workspace_layout(pl->P, &pl->L);
         workspace_image(pl->P, pl->L, &img);
-        e = lib_malloc(reinterpret_cast<void**>(&pl->ws), pl->L.bytes);
+        e = lib_malloc(reinterpret_cast<void**>(&pl->ws), pl->L.total);
         if (e != cudaSuccess) rc = cuda_fail(e, "plan workspace");
     }
     if (!rc) {
