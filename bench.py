@@ -194,7 +194,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons, "samples": len(self.rows)}
 
 
 def tail_neff(N, lw, specs, tail_N):
@@ -824,11 +824,12 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            nat.fpt_simulate_batch_host(pe, sets, i, hN, hl, hb, hc)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        with ClockSampler(local) as clk_e:
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                nat.fpt_simulate_batch_host(pe, sets, i, hN, hl, hb, hc)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
         tt = torch.tensor([dt, float(steps_ctr.item())], dtype=torch.float64, device=dev)
         if world > 1:
             t1 = tt.clone()
@@ -853,7 +854,8 @@ def main():
         e2e = {"value": es / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_call": dt / args.steps * 1e3,
                "records_d2h_ms": link_s * 1e3, "records_d2h_gbs": 16 * n / link_s / 1e9,
-               "copies": "records on a second stream during the histogram kernels, then bins and counters"}
+               "copies": "records on a second stream during the histogram kernels, then bins and counters",
+               "clocks": clk_e.summary()}
 
     if rank != 0:
         if world > 1:
