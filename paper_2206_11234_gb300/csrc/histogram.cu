@@ -3,12 +3,14 @@
 //
 // Per bin: n_j, max ln w and, with x = ln w - max <= 0, s1 = sum exp(x),
 // s2 = sum exp(2 x), l_k = sum x^k for k = 1..4 (the moments of ln w behind the
-// lognormal estimator and normality test of §2.4).  Two streaming passes over the 16-byte
-// records (the data is HBM-resident and read twice; at ~7 TB/s that is well
-// under a millisecond for 10^7 records):
-//   pass 1: classify each record, per-bin max of ln w (shared-memory atomicMax
-//           on an order-preserving 64-bit key, one global atomic per bin and block);
-//   pass 2: max-shifted sums into shared-memory bins, lanes of a warp that hit
+// lognormal estimator and normality test of §2.4).  Two streaming passes over the
+// records (HBM-resident; the passes are bound by the binary64 arithmetic, not
+// by the bytes):
+//   pass 1: classify each record (16 B read), per-bin max of ln w (shared-memory
+//           atomicMax on an order-preserving 64-bit key, one global atomic per bin
+//           and block); with a bin-index buffer, store each record's bin (4 B);
+//   pass 2: read ln w and the stored bin (or classify again without the buffer),
+//           max-shifted sums into shared-memory bins, lanes of a warp that hit
 //           the same bin (__match_any_sync) combined by their lowest lane, one
 //           peer per shuffle round, before one shared atomic per bin and warp.
 // Bins are right-closed: j = ceil((N - lo)/d) - 1, clamped to [0, n_bins).
