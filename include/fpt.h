@@ -172,7 +172,11 @@ typedef struct fpt_hist_counts {
  * set s fills out_bins[boff_s .. boff_s + n_bins_s), boff_s = sum_{t<s} n_bins_t,
  * and out_counts[s] (device).
  * sets: host array, 1 <= n_sets <= FPT_MAX_SETS; p->set_id and p->traj_offset
- * are ignored (each set carries its own). */
+ * are ignored (each set carries its own).
+ * Device memory: the call takes a stream-ordered workspace from the library's
+ * pool (the set table and scratch, and with bins 4 bytes per run for the bin
+ * index of the histogram's first pass) and returns it before returning; the
+ * pool keeps it mapped for the next call.  FPT_ENOMEM if it cannot be had. */
 int fpt_simulate_batch(const fpt_params* p, const fpt_set* sets, int32_t n_sets, uint64_t seed,
                        double* out_N, double* out_logw, fpt_bin* out_bins,
                        fpt_hist_counts* out_counts);
@@ -199,7 +203,9 @@ int fpt_plan_destroy(fpt_plan* plan);
  * Record i (global id id_offset + i) goes to subset (id_offset + i) mod n_sub
  * (jackknife subsets, §2.1); bins[s * n_bins + j].  The outputs are
  * overwritten.  1 <= n_bins, 1 <= n_sub, n_sub * n_bins <= FPT_MAX_HIST_BINS,
- * lo < hi finite. */
+ * lo < hi finite.  Device memory: a workspace of 4 bytes per record (the bin
+ * index of the first pass) and a few hundred bytes from the library's pool,
+ * returned before the call returns; FPT_ENOMEM if it cannot be had. */
 int fpt_histogram(const double* N, const double* logw, int64_t n, int32_t n_bins, double lo,
                   double hi, int32_t n_sub, uint64_t id_offset, fpt_bin* bins,
                   fpt_hist_counts* counts, void* stream);
